@@ -1,0 +1,196 @@
+"""Pins of the oracle's optimisers (Sec. 5, Algorithm 1) against values the
+paper or the mathematics fixes: the harmonic ground-state energy d/2, the
+reduction to the scalar GPE, the exact Zeeman shift, the M <-> -M symmetry,
+monotone ARNT energies, spectral prolongation, and the ground-state energies
+printed in the paper's Sec. 7.2 / 7.3 tables (tests/golden)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sbec_oracle as O
+from paper_1907_01194_gb300 import workloads as W
+from tests.conftest import golden
+from tests.oracle_helpers import (oracle_problem, paper_spin2_1d, paper_spin3_1d,
+                                  small_workload)
+
+
+def _solve(P, X0, tol=1e-10, **kw):
+    Xs, st, _ = O.solve(P, X0, O.SolveOptions(tol=tol, **kw))
+    return Xs, st
+
+
+def _scalar_ground_energy(n, L, V, beta0):
+    """Scalar GPE ground state by the backward-Euler normalised gradient flow
+    x <- (I + tau H(x))^{-1} x / ||.||, H(x) = L/2 + V + (beta0/h) |x|^2, with a dense
+    Laplacian; an algorithm independent of the Riemannian solver."""
+    h = 2 * L / n
+    Lm = np.real(O.dense_laplacian_1d(n, -L, L))
+    x = np.exp(-(np.linspace(-L, L, n, endpoint=False)) ** 2 / 2)
+    x /= np.linalg.norm(x)
+    tau = 0.5
+    for _ in range(5000):
+        H = 0.5 * Lm + np.diag(V + beta0 / h * x ** 2)
+        xn = np.linalg.solve(np.eye(n) + tau * H, x)
+        xn /= np.linalg.norm(xn)
+        Hx = (0.5 * Lm + np.diag(V + beta0 / h * xn ** 2)) @ xn
+        mu = xn @ Hx
+        x = xn
+        if np.linalg.norm(Hx - mu * xn) < 1e-11:
+            break
+    return 0.5 * x @ Lm @ x + x @ (V * x) + beta0 / (2 * h) * np.sum(x ** 4)
+
+
+@pytest.mark.parametrize("F,n,L,M", [(1, (64,), 8.0, 0.3), (3, (64,), 8.0, 1.4)])
+def test_harmonic_ground_state_is_d_over_2(F, n, L, M):
+    w = small_workload(F, n, L=L, beta=(0.0, 0.0, 0.0, 0.0), M=M)
+    P = oracle_problem(w)
+    Xs, st = _solve(P, O.to_matrix(P, W.initial_fields(w)))
+    assert st.converged
+    assert abs(st.energy - len(n) / 2) < 1e-10
+
+
+@pytest.mark.parametrize("F,n,L,M", [(3, (64, 64), 8.0, 0.6), (1, (64, 64, 64), 8.0, 0.4)])
+def test_harmonic_gaussian_spinor_is_stationary(F, n, L, M):
+    # beta = 0: Phi = U pi^{-d/4} exp(-|x|^2/2) with U on the constraint set is a
+    # ground state, so its Riemannian gradient vanishes and E = d/2 (2D and 3D)
+    w = small_workload(F, n, L=L, beta=(0.0, 0.0, 0.0, 0.0), M=M)
+    P = oracle_problem(w)
+    d = len(n)
+    r2 = sum(np.meshgrid(*[x ** 2 for x in reversed(P.grid_axes())], indexing="ij"))
+    phi = np.pi ** (-d / 4) * np.exp(-r2 / 2)
+    U = np.zeros(P.C)
+    U[0], U[-1] = math.sqrt((1 + M / F) / 2), math.sqrt((1 - M / F) / 2)   # masses at l = +-F
+    X = math.sqrt(P.dV) * phi.reshape(-1)[:, None] * U[None, :]
+    u = O.to_u(P, X)
+    assert abs(O.E_u(P, u) - d / 2) < 1e-10
+    assert np.linalg.norm(O.rgrad(P, u)) < 1e-9
+
+
+@pytest.mark.parametrize("F,M", [(1, 0.2), (1, 0.7), (2, 0.3), (2, 1.2)])
+def test_reduces_to_scalar_gpe(F, M):
+    # beta1 = beta2 = beta3 = 0, p = q = 0: E_g does not depend on M and equals the
+    # scalar ground energy with the same beta0 (Sec. 2, M = +-F remark)
+    n, L, b0 = 64, 8.0, 20.0
+    w = small_workload(F, (n,), L=L, beta=(b0, 0.0, 0.0, 0.0), M=M)
+    P = oracle_problem(w)
+    Xs, st = _solve(P, O.to_matrix(P, W.initial_fields(w)))
+    assert st.converged
+    ref = _scalar_ground_energy(n, L, W.potential(w), b0)
+    assert abs(st.energy - ref) < 1e-9
+
+
+def test_linear_zeeman_shift_is_exact():
+    # the linear Zeeman term integrates to -p M on M, so E_g(p) = E_g(0) - p M
+    p, M = 0.25, 0.4
+    w0 = small_workload(2, (64,), beta=(30.0, -1.0, 2.0, 0.0), M=M)
+    wp = small_workload(2, (64,), beta=(30.0, -1.0, 2.0, 0.0), M=M, p=p)
+    P0, Pp = oracle_problem(w0), oracle_problem(wp)
+    X0 = O.to_matrix(P0, W.initial_fields(w0))
+    _, s0 = _solve(P0, X0)
+    _, sp = _solve(Pp, X0)
+    assert abs(sp.energy - (s0.energy - p * M)) < 1e-9
+
+
+def test_magnetisation_sign_symmetry():
+    # M <-> -M with phi_l <-> phi_{-l} (Sec. 4)
+    wp = small_workload(2, (48,), beta=(30.0, 2.0, -3.0, 0.0), M=0.5)
+    wm = small_workload(2, (48,), beta=(30.0, 2.0, -3.0, 0.0), M=-0.5)
+    Pp, Pm = oracle_problem(wp), oracle_problem(wm)
+    X0 = O.to_matrix(Pp, W.initial_fields(wp))
+    _, sp = _solve(Pp, X0)
+    _, sm = _solve(Pm, X0[:, ::-1].copy())
+    assert abs(sp.energy - sm.energy) < 1e-10
+
+
+def test_arnt_energy_monotone_and_constraints_kept():
+    w = small_workload(3, (48,), beta=(60.0, -1.0, 4.0, 1.0), M=0.8)
+    P = oracle_problem(w)
+    Xs, st = _solve(P, O.to_matrix(P, W.initial_fields(w)), tol=1e-9)
+    assert st.converged
+    E = [e for (kind, e, g) in st.history if kind == "arnt"]
+    assert all(b <= a + 1e-12 for a, b in zip(E, E[1:]))
+    N, Mag = O.constraints(P, Xs)
+    assert abs(N - 1) < 1e-12 and abs(Mag - 0.8) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_rgbb_reaches_same_minimum(kind):
+    w = small_workload(1, (48,), beta=(30.0, -1.0, 0.0, 0.0), M=0.3)
+    P = oracle_problem(w)
+    X0 = O.to_matrix(P, W.initial_fields(w))
+    _, s_arnt = _solve(P, X0, tol=1e-9)
+    _, s_rgbb = _solve(P, X0, tol=1e-7, method="rgbb", retraction=kind)
+    assert s_rgbb.converged
+    assert abs(s_rgbb.energy - s_arnt.energy) < 1e-10
+
+
+def test_prolongation_is_exact_on_band_limited_fields():
+    wc = small_workload(1, (16, 8), L=4.0)
+    wf = small_workload(1, (32, 16), L=4.0)
+    Pc, Pf = oracle_problem(wc), oracle_problem(wf)
+
+    def field(P):
+        y, x = np.meshgrid(*reversed(P.grid_axes()), indexing="ij")
+        f = (1.0 + 0.3 * np.cos(2 * np.pi * x / 8) + 0.2 * np.sin(2 * np.pi * 3 * y / 8)
+             + 0.1j * np.cos(2 * np.pi * 2 * (x + y) / 8))
+        return f.reshape(-1)
+
+    Xc = np.stack([field(Pc) * a for a in (0.5, 0.3, 0.2)], axis=1) * math.sqrt(Pc.dV)
+    uc = O.psi_R1(Pc, O.to_u(Pc, Xc))
+    Xc = O.from_u(Pc, uc)
+    Xf = O.prolongate(Pc, Pf, Xc)
+    # the band-limited coarse state is reproduced exactly (up to the common scale)
+    ref = np.stack([field(Pf) for _ in range(3)], axis=1)
+    ratio = Xf / ref
+    assert np.allclose(ratio, ratio[0:1, :], atol=1e-13)
+    N, Mag = O.constraints(Pf, Xf)
+    assert abs(N - 1) < 1e-13 and abs(Mag - Pc.M) < 1e-13
+
+
+def test_cascadic_matches_direct_solve():
+    w = small_workload(1, (64,), beta=(40.0, -1.0, 0.0, 0.0), M=0.25)
+    levels = [oracle_problem(w.at((16,))), oracle_problem(w.at((32,))), oracle_problem(w)]
+    Xc0 = O.to_matrix(levels[0], W.initial_fields(w.at((16,))))
+    Xs, st, stats = O.solve(levels, Xc0, O.SolveOptions(tol=1e-10))
+    P = levels[-1]
+    _, sd = _solve(P, O.to_matrix(P, W.initial_fields(w)))
+    assert st.converged and abs(st.energy - sd.energy) < 1e-10
+
+
+SPIN2 = [(int(c), float(M), float(E)) for c, M, E in golden("spin2_1d_energies.txt")]
+
+
+@pytest.mark.parametrize("case,M,E_paper", [r for r in SPIN2 if not (r[0] == 3 and r[1] == 0.0)])
+def test_paper_spin2_1d_ten_digit_energies(case, M, E_paper):
+    P, X0 = paper_spin2_1d(case, M)
+    _, st = _solve(P, X0, tol=1e-9)
+    assert st.converged
+    assert abs(st.energy - E_paper) < 1e-9
+
+
+def test_paper_spin2_1d_cyclic_M0_reaches_scalar_lower_bound():
+    # Case III, M = 0: the spinor (1/3, 2/3 masses in l = 2, -1) makes F and A00
+    # vanish pointwise, so E_g equals the scalar GPE energy, a lower bound for
+    # beta1, beta2 >= 0; the oracle reaches it, below the printed 24.1143586550.
+    P, X0 = paper_spin2_1d(3, 0.0)
+    _, st = _solve(P, X0, tol=1e-9)
+    printed = [E for c, M, E in SPIN2 if c == 3 and M == 0.0][0]
+    ref = _scalar_ground_energy(512, 16.0, P.V.reshape(-1), 183.9)
+    assert st.converged
+    assert abs(st.energy - ref) < 1e-8
+    assert st.energy < printed
+
+
+SPIN3 = [(int(c), float(M), float(E)) for c, M, E in golden("spin3_1d_energies.txt")]
+
+
+@pytest.mark.parametrize("case,M,E_paper", SPIN3)
+def test_paper_spin3_1d_table_energies(case, M, E_paper):
+    # Case II has phi_0 != 0 at M = 0, which pins the printed A_0 (psi_0^2 coefficient
+    # sqrt2/sqrt21) against the Clebsch-Gordan-normalised 2/sqrt21 (that variant gives
+    # 17.2572 here).
+    P, X0 = paper_spin3_1d(case, M, seed=0)
+    _, st = _solve(P, X0, tol=1e-8)
+    assert st.converged
+    assert abs(st.energy - E_paper) <= 5.001e-5
