@@ -1,0 +1,142 @@
+/*
+ * libsbec — C ABI of the GB300 (sm_103a) kernels for the spin-F BEC
+ * ground-state problem of Tian, Cai, Wu & Wen, "Ground states and their
+ * characterization of spin-F Bose-Einstein condensates" (arXiv:1907.01194).
+ *
+ * Problem (Sec. 3, Eq. minimize:discrete): minimise the Fourier-pseudospectral
+ * Gross-Pitaevskii energy E_h(X) over X in C^{G x (2F+1)} subject to
+ * tr(X^* X) = 1 and tr(X^* X D) = M, the manifold M of Sec. 4.
+ *
+ * State layout (all calls): X is the paper's scaled variable X = sqrt(dV) phi,
+ * dV = prod_i h_i, stored component-major as [C][n_z][n_y][n_x] (x fastest),
+ * components ordered l = F, F-1, ..., -F, interleaved complex: double2
+ * (precision SBEC_FP64) or float2 (SBEC_MIXED).  Grid points are
+ * x_j = lo + j (hi - lo) / n, j = 0..n-1, on each axis (Sec. 3).  n_i is a
+ * power of two, 2 <= n_i <= 1024; missing axes of 1D/2D problems have n = 1.
+ *
+ * Pointers: every array argument may be a device pointer or a host pointer
+ * (pageable or pinned); host arrays are staged through the handle's
+ * workspace with copies on the handle's stream.  The caller owns all state
+ * arrays; the library owns its workspace (allocated by sbec_create, freed by
+ * sbec_destroy).  No other call allocates memory.
+ *
+ * Ordering and synchronisation: every call is ordered on the handle's stream.
+ * A call that returns scalars through host pointers (non-NULL double* outputs)
+ * or that reads/writes host arrays synchronises the stream before returning.
+ * A call with only device arrays and NULL scalar outputs is asynchronous; its
+ * scalar results stay in the handle's device scalar block (sbec_scalars) and
+ * any device-side error is recorded there and reported by sbec_sync.
+ *
+ * Errors: every call returns SBEC_OK or one of the codes below; no call
+ * aborts or throws across the ABI.
+ */
+#ifndef SBEC_H
+#define SBEC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBEC_OK             0
+#define SBEC_ERR_ARG        1  /* bad argument: |M| >= F, F not in {1,2,3}, bad n, NULL */
+#define SBEC_ERR_DOMAIN     2  /* point outside the retraction's domain (Omega or S),
+                                  u^T Gamma^2 u - M^2 <= 0, or root bracket failure */
+#define SBEC_ERR_NONFINITE  3  /* NaN or Inf in a reduction */
+#define SBEC_ERR_CUDA       4  /* a CUDA runtime call failed */
+#define SBEC_ERR_TIMEOUT    5  /* a bounded device-side wait expired */
+#define SBEC_ERR_NOCONV     6  /* solver hit its iteration cap; the state is still written */
+
+#define SBEC_FP64   0          /* every step in double precision */
+#define SBEC_MIXED  1          /* FFT and pointwise steps in float, reductions and
+                                  retraction scalars in double (state is float2) */
+
+/* Problem statement (Sec. 2-3).  beta[0..3] = (beta0, beta1, beta2, beta3):
+ * density, spin, singlet (F >= 2) and quintet (F = 3) interaction strengths;
+ * p, q: linear and quadratic Zeeman shifts (b_l = -p l + q l^2); M: the
+ * magnetisation; lo/hi: the box per axis (x, y, z). */
+typedef struct sbec_problem {
+    int    F;            /* spin: 1, 2 or 3 (C = 2F+1 components) */
+    int    dim;          /* 1, 2 or 3 */
+    int    n[3];         /* grid points per axis (x, y, z); unused axes: 1 */
+    double lo[3], hi[3]; /* box per axis */
+    double beta[4];
+    double p, q;
+    double M;
+    int    precision;    /* SBEC_FP64 or SBEC_MIXED */
+} sbec_problem;
+
+typedef struct sbec_handle sbec_handle;
+
+/* Create a handle for one problem on the calling thread's current device.
+ * V: potential at the grid points, G doubles in [n_z][n_y][n_x] order (host or
+ * device; copied), or NULL for the harmonic trap V = |x|^2 / 2.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ * Allocates the workspace (about 5 C G complex values plus V). */
+int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sbec_handle** out);
+int sbec_destroy(sbec_handle* h);
+
+/* E_h(X), Eq. (3.7) with h -> dV.  E: host pointer or NULL (then the value is
+ * left in the scalar block, slot SBEC_S_ENERGY). */
+int sbec_energy(sbec_handle* h, const void* X, double* E);
+
+/* Euclidean gradient nabla E_h(X) w.r.t. Re<.,.> (Eq. 3.12) into G_euc, and
+ * the Riemannian gradient grad E = P_u nabla E (Eq. 4.6, Lemma 4.1) into
+ * G_riem, with u the real stacking of X (Sec. 4).  Either output may be NULL.
+ * E and rgrad_norm (||grad E||_2, the stopping norm of Sec. 7.1) are optional
+ * host outputs.  The Lemma 4.1 coefficients are cached in the handle for the
+ * next sbec_hessvec with riemannian != 0. */
+int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* E,
+              double* rgrad_norm);
+
+/* Hessian-vector product.  riemannian == 0: HZ = nabla^2 E_h(X)[Z] + sigma Z
+ * (Eq. 3.13).  riemannian != 0: HZ = Hess f(u)[xi] of Lemma 4.2 for
+ * f = E + (sigma/2)||u - u_k||^2, i.e. P_u(nabla^2 E[xi] + sigma xi
+ * - alpha_g xi - beta_g Gamma xi) with xi = P_u Z, using the alpha_g, beta_g
+ * of the latest sbec_grad call at the same X (the call recomputes them when
+ * X differs from that call's pointer). */
+int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int riemannian,
+                 void* HZ);
+
+/* Retraction R_u(t xi) = psi(u + t xi) (Sec. 6, Eq. oretr0): kind 1 = projective
+ * (Lemma 5.1), 2 = orthogonal (Lemma 5.3), 3 = closed form (Lemma 5.4).
+ * out may alias U.  Returns SBEC_ERR_DOMAIN (synchronous calls) when u + t xi
+ * is outside Omega (kinds 1, 2) or S (kind 3). */
+int sbec_retract(sbec_handle* h, const void* U, const void* Xi, double t, int kind, void* out);
+
+/* Stream synchronisation; returns the first device-side error recorded since
+ * the previous sbec_sync (and clears it), or SBEC_ERR_CUDA. */
+int sbec_sync(sbec_handle* h);
+
+/* Device pointer to the handle's scalar block (doubles, see SBEC_S_* slots). */
+const double* sbec_scalars(const sbec_handle* h);
+
+/* Launch bookkeeping (not in the paper: instrumentation of this library).
+ * sbec_launch_count: number of library kernels launched on the handle so far.
+ * sbec_profile(h, 1) starts recording a CUDA event pair around every kernel
+ * launch on the handle's stream (at most 16384 launches; later ones are
+ * counted but not timed); sbec_profile(h, 0) stops.  sbec_profile_read
+ * synchronises the stream, adds the recorded device times per kernel and
+ * returns up to `max` rows: names (NUL-terminated, 32 bytes each in
+ * `names`), total milliseconds and launch counts; *rows receives the row
+ * count.  Reading clears the recorded launches. */
+long long sbec_launch_count(const sbec_handle* h);
+int sbec_profile(sbec_handle* h, int enable);
+int sbec_profile_read(sbec_handle* h, int max, char* names, double* ms, long long* counts, int* rows);
+
+#define SBEC_S_ENERGY      0   /* E_h of the latest energy / grad call */
+#define SBEC_S_RGRAD_NORM2 1   /* ||grad E||^2 of the latest grad call */
+#define SBEC_S_ALPHA_G     2   /* Lemma 4.2 alpha_g of the latest grad call */
+#define SBEC_S_BETA_G      3   /* Lemma 4.2 beta_g */
+#define SBEC_S_MASS        4   /* u^T u of the latest grad call */
+#define SBEC_S_MAG         5   /* u^T Gamma u */
+#define SBEC_S_STATUS      6   /* device-side error code (as double) */
+
+const char* sbec_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBEC_H */

@@ -1,0 +1,406 @@
+// libsbec C ABI: handle management, argument checking, host/device staging and
+// dispatch to the per-precision kernel orchestration.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "sbec.h"
+#include "sbec_internal.h"
+
+struct sbec_handle {
+    sbec_problem prob;
+    sbec::Geom geom;
+    sbec::Work work;
+    cudaStream_t stream;
+    int device;
+    size_t elem;          // bytes of one complex value
+    size_t field_bytes;   // C * G * elem
+    void* d_tw;
+    double* d_lam2;
+    void* d_V;
+    void* stage[3];
+    double* h_scal;       // pinned mirror of the scalar block
+    const void* last_grad_X;
+    sbec::Prof prof;
+};
+
+namespace sbec {
+
+void prof_begin(Prof* p, int kid, cudaStream_t s) {
+    if (!p) return;
+    ++p->launches;
+    if (p->enabled && p->nrec < p->cap) {
+        cudaEventRecord(p->ev[2 * p->nrec], s);
+        p->kid[p->nrec] = kid;
+    }
+}
+
+void prof_end(Prof* p, cudaStream_t s) {
+    if (!p) return;
+    if (p->enabled && p->nrec < p->cap) {
+        cudaEventRecord(p->ev[2 * p->nrec + 1], s);
+        ++p->nrec;
+    }
+}
+
+}  // namespace sbec
+
+namespace {
+
+bool is_pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+#define TRY_CUDA(expr)                                          \
+    do {                                                        \
+        if ((expr) != cudaSuccess) { cudaGetLastError(); return SBEC_ERR_CUDA; } \
+    } while (0)
+
+int read_scalars(sbec_handle* h) {
+    TRY_CUDA(cudaMemcpyAsync(h->h_scal, h->work.scal, sbec::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+    TRY_CUDA(cudaStreamSynchronize(h->stream));
+    const int st = (int)h->h_scal[SBEC_S_STATUS];
+    if (st != 0) {
+        const double zero = 0.0;
+        TRY_CUDA(cudaMemcpyAsync(h->work.scal + SBEC_S_STATUS, &zero, sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream));
+        TRY_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return st;
+}
+
+// Resolve an input array: device pointers pass through, host arrays are copied
+// into staging buffer `slot`.
+int stage_in(sbec_handle* h, const void* p, int slot, const void** out, bool* host) {
+    if (!p) { *out = nullptr; return SBEC_ERR_ARG; }
+    if (is_device_ptr(p)) { *out = p; return SBEC_OK; }
+    *host = true;
+    TRY_CUDA(cudaMemcpyAsync(h->stage[slot], p, h->field_bytes, cudaMemcpyHostToDevice, h->stream));
+    *out = h->stage[slot];
+    return SBEC_OK;
+}
+
+void* stage_out_ptr(sbec_handle* h, void* p, int slot, bool* host) {
+    if (!p) return nullptr;
+    if (is_device_ptr(p)) return p;
+    *host = true;
+    return h->stage[slot];
+}
+
+int copy_back(sbec_handle* h, void* user, void* dev) {
+    if (user && user != dev) TRY_CUDA(cudaMemcpyAsync(user, dev, h->field_bytes, cudaMemcpyDeviceToHost, h->stream));
+    return SBEC_OK;
+}
+
+void free_handle(sbec_handle* h) {
+    if (!h) return;
+    cudaFree(h->d_tw);
+    cudaFree(h->d_lam2);
+    cudaFree(h->d_V);
+    cudaFree(h->work.work);
+    cudaFree(h->work.work2);
+    cudaFree(h->work.partA);
+    cudaFree(h->work.partB);
+    cudaFree(h->work.scal);
+    for (int i = 0; i < 3; ++i) cudaFree(h->stage[i]);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    if (h->prof.ev) {
+        for (int i = 0; i < 2 * h->prof.cap; ++i) cudaEventDestroy(h->prof.ev[i]);
+        free(h->prof.ev);
+        free(h->prof.kid);
+    }
+    free(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbec_status_string(int s) {
+    switch (s) {
+        case SBEC_OK: return "ok";
+        case SBEC_ERR_ARG: return "invalid argument";
+        case SBEC_ERR_DOMAIN: return "point outside the domain of the retraction or projection";
+        case SBEC_ERR_NONFINITE: return "non-finite value in a reduction";
+        case SBEC_ERR_CUDA: return "CUDA runtime error";
+        case SBEC_ERR_TIMEOUT: return "bounded device wait expired";
+        case SBEC_ERR_NOCONV: return "iteration cap reached before the tolerance";
+        default: return "unknown status";
+    }
+}
+
+int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sbec_handle** out) {
+    if (!prob || !out) return SBEC_ERR_ARG;
+    *out = nullptr;
+    const sbec_problem& P = *prob;
+    if (P.F < 1 || P.F > 3 || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
+    if (P.precision != SBEC_FP64 && P.precision != SBEC_MIXED) return SBEC_ERR_ARG;
+    if (!(fabs(P.M) < (double)P.F)) return SBEC_ERR_ARG;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax < P.dim) {
+            if (!is_pow2(P.n[ax]) || P.n[ax] < 2 || P.n[ax] > 1024) return SBEC_ERR_ARG;
+            if (!(P.hi[ax] > P.lo[ax])) return SBEC_ERR_ARG;
+        } else if (P.n[ax] != 1) {
+            return SBEC_ERR_ARG;
+        }
+    }
+    sbec_handle* h = (sbec_handle*)calloc(1, sizeof(sbec_handle));
+    if (!h) return SBEC_ERR_CUDA;
+    h->prob = P;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->work.prof = &h->prof;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return SBEC_ERR_CUDA; }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->work.num_sms = sms > 0 ? sms : 1;
+
+    sbec::Geom& g = h->geom;
+    g.F = P.F; g.C = 2 * P.F + 1; g.dim = P.dim;
+    double dV = 1.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        g.n[ax] = P.n[ax];
+        g.logn[ax] = ilog2(P.n[ax]);
+        if (ax < P.dim) dV *= (P.hi[ax] - P.lo[ax]) / P.n[ax];
+    }
+    g.G = (long long)P.n[0] * P.n[1] * P.n[2];
+    g.dV = dV;
+    g.invG = 1.0 / (double)g.G;
+    g.M = P.M;
+    for (int i = 0; i < 7; ++i) {
+        const double l = (double)(P.F - i);
+        g.bz[i] = (i < g.C) ? (-P.p * l + P.q * l * l) : 0.0;
+    }
+    const double b0 = P.beta[0], b1 = P.beta[1];
+    const double b2 = P.F >= 2 ? P.beta[2] : 0.0, b3 = P.F == 3 ? P.beta[3] : 0.0;
+    g.g0 = 2 * b0 / dV; g.g1 = 2 * b1 / dV; g.g2 = 2 * b2 / dV; g.g3 = 2 * b3 / dV;
+    g.e0 = b0 / (2 * dV); g.e1 = b1 / (2 * dV); g.e2 = b2 / (2 * dV); g.e3 = b3 / (2 * dV);
+
+    const bool dbl = P.precision == SBEC_FP64;
+    h->elem = dbl ? 2 * sizeof(double) : 2 * sizeof(float);
+    h->field_bytes = (size_t)g.C * (size_t)g.G * h->elem;
+    const size_t real_bytes = dbl ? sizeof(double) : sizeof(float);
+    const size_t ntw = (size_t)P.n[0] + P.n[1] + P.n[2];
+    const size_t part = dbl ? sbec::Ops<double>::partials_needed(g, h->work.num_sms)
+                            : sbec::Ops<float>::partials_needed(g, h->work.num_sms);
+    h->work.part_cap = part;
+
+    bool ok = true;
+    ok = ok && cudaMalloc(&h->d_tw, ntw * h->elem) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->d_lam2, ntw * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->d_V, (size_t)g.G * real_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->work.work, h->field_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->work.work2, h->field_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->work.partA, part * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->work.partB, part * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->work.scal, sbec::S_COUNT * sizeof(double)) == cudaSuccess;
+    for (int i = 0; i < 3; ++i) ok = ok && cudaMalloc(&h->stage[i], h->field_bytes) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->h_scal, sbec::S_COUNT * sizeof(double)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }
+
+    // lambda_p^2 = (2 pi p / (b - a))^2 with p the signed DFT frequency (Eq. 3.6)
+    double* lam = (double*)malloc(ntw * sizeof(double));
+    size_t off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int n = P.n[ax];
+        for (int j = 0; j < n; ++j) {
+            const int p = (j < n / 2) ? j : j - n;
+            const double L = (ax < P.dim) ? (P.hi[ax] - P.lo[ax]) : 1.0;
+            const double lamp = (n > 1) ? 2.0 * M_PI * (double)p / L : 0.0;
+            lam[off + j] = lamp * lamp;
+        }
+        g.lam2[ax] = h->d_lam2 + off;
+        off += n;
+    }
+    cudaError_t ce = cudaMemcpyAsync(h->d_lam2, lam, ntw * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    free(lam);
+    if (ce != cudaSuccess) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }
+    if (cudaMemsetAsync(h->work.scal, 0, sbec::S_COUNT * sizeof(double), h->stream) != cudaSuccess) {
+        free_handle(h);
+        return SBEC_ERR_CUDA;
+    }
+
+    g.V = h->d_V;
+    int st = dbl ? sbec::Ops<double>::init_tables(g, h->d_tw, h->stream)
+                 : sbec::Ops<float>::init_tables(g, h->d_tw, h->stream);
+    if (st == SBEC_OK) {
+        if (V == nullptr) {
+            st = dbl ? sbec::Ops<double>::harmonic_potential(g, h->d_V, P.lo, P.hi, h->stream)
+                     : sbec::Ops<float>::harmonic_potential(g, h->d_V, P.lo, P.hi, h->stream);
+        } else {
+            // copy the caller's potential (host or device) through a staging field
+            const double* Vd = V;
+            void* tmp = h->stage[0];
+            if (!is_device_ptr(V)) {
+                if (cudaMemcpyAsync(tmp, V, (size_t)g.G * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+                    cudaSuccess) st = SBEC_ERR_CUDA;
+                Vd = (const double*)tmp;
+            }
+            if (st == SBEC_OK)
+                st = dbl ? sbec::Ops<double>::convert_potential(g, h->d_V, Vd, h->stream)
+                         : sbec::Ops<float>::convert_potential(g, h->d_V, Vd, h->stream);
+        }
+    }
+    if (st == SBEC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = SBEC_ERR_CUDA;
+    if (st != SBEC_OK) { cudaGetLastError(); free_handle(h); return st; }
+    *out = h;
+    return SBEC_OK;
+}
+
+int sbec_destroy(sbec_handle* h) {
+    if (!h) return SBEC_ERR_ARG;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+    return SBEC_OK;
+}
+
+int sbec_sync(sbec_handle* h) {
+    if (!h) return SBEC_ERR_ARG;
+    return read_scalars(h);
+}
+
+const double* sbec_scalars(const sbec_handle* h) { return h ? h->work.scal : nullptr; }
+
+long long sbec_launch_count(const sbec_handle* h) { return h ? h->prof.launches : -1; }
+
+static const char* kKernelNames[sbec::K_COUNT] = {
+    "x_fwd", "x_fwd_energy", "x_inv_grad", "x_inv_hess", "x_full_grad", "x_full_energy", "x_full_hess",
+    "s_fwd", "s_inv", "s_k2", "s_parseval", "dot_reduce", "proj_apply", "retract_w", "scale", "finalize",
+    "retract_solve", "tables"};
+
+int sbec_profile(sbec_handle* h, int enable) {
+    if (!h) return SBEC_ERR_ARG;
+    sbec::Prof& p = h->prof;
+    if (enable && !p.ev) {
+        p.cap = 16384;
+        p.ev = (cudaEvent_t*)calloc(2 * p.cap, sizeof(cudaEvent_t));
+        p.kid = (int*)calloc(p.cap, sizeof(int));
+        if (!p.ev || !p.kid) return SBEC_ERR_CUDA;
+        for (int i = 0; i < 2 * p.cap; ++i) TRY_CUDA(cudaEventCreate(&p.ev[i]));
+    }
+    if (enable) {
+        p.nrec = 0;
+        for (int k = 0; k < sbec::K_COUNT; ++k) { p.ms[k] = 0.0; p.cnt[k] = 0; }
+    }
+    p.enabled = enable ? 1 : 0;
+    return SBEC_OK;
+}
+
+int sbec_profile_read(sbec_handle* h, int max, char* names, double* ms, long long* counts, int* rows) {
+    if (!h || !rows) return SBEC_ERR_ARG;
+    sbec::Prof& p = h->prof;
+    TRY_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < p.nrec; ++i) {
+        float t = 0.f;
+        TRY_CUDA(cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]));
+        p.ms[p.kid[i]] += t;
+        p.cnt[p.kid[i]] += 1;
+    }
+    p.nrec = 0;
+    int r = 0;
+    for (int k = 0; k < sbec::K_COUNT && r < max; ++k) {
+        if (p.cnt[k] == 0) continue;
+        if (names) { strncpy(names + 32 * r, kKernelNames[k], 31); names[32 * r + 31] = 0; }
+        if (ms) ms[r] = p.ms[k];
+        if (counts) counts[r] = p.cnt[k];
+        ++r;
+    }
+    for (int k = 0; k < sbec::K_COUNT; ++k) { p.ms[k] = 0.0; p.cnt[k] = 0; }
+    *rows = r;
+    return SBEC_OK;
+}
+
+int sbec_energy(sbec_handle* h, const void* X, double* E) {
+    if (!h || !X) return SBEC_ERR_ARG;
+    bool host = false;
+    const void* Xd;
+    int st = stage_in(h, X, 0, &Xd, &host);
+    if (st) return st;
+    st = h->prob.precision == SBEC_FP64 ? sbec::Ops<double>::energy(h->geom, h->work, Xd, h->stream)
+                                        : sbec::Ops<float>::energy(h->geom, h->work, Xd, h->stream);
+    if (st) return st;
+    if (E || host) {
+        st = read_scalars(h);
+        if (E) *E = h->h_scal[SBEC_S_ENERGY];
+    }
+    return st;
+}
+
+int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* E, double* rgrad_norm) {
+    if (!h || !X) return SBEC_ERR_ARG;
+    bool host = false;
+    const void* Xd;
+    int st = stage_in(h, X, 0, &Xd, &host);
+    if (st) return st;
+    void* ge = stage_out_ptr(h, G_euc, 1, &host);
+    void* gr = stage_out_ptr(h, G_riem, 2, &host);
+    st = h->prob.precision == SBEC_FP64
+             ? sbec::Ops<double>::grad(h->geom, h->work, Xd, ge, gr, rgrad_norm != nullptr, h->stream)
+             : sbec::Ops<float>::grad(h->geom, h->work, Xd, ge, gr, rgrad_norm != nullptr, h->stream);
+    if (st) return st;
+    h->last_grad_X = host ? nullptr : X;
+    if ((st = copy_back(h, G_euc, ge))) return st;
+    if ((st = copy_back(h, G_riem, gr))) return st;
+    if (E || rgrad_norm || host) {
+        st = read_scalars(h);
+        if (E) *E = h->h_scal[SBEC_S_ENERGY];
+        if (rgrad_norm) *rgrad_norm = sqrt(h->h_scal[SBEC_S_RGRAD_NORM2]);
+    }
+    return st;
+}
+
+int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int riemannian, void* HZ) {
+    if (!h || !X || !Z || !HZ) return SBEC_ERR_ARG;
+    bool host = false;
+    const void *Xd, *Zd;
+    int st = stage_in(h, X, 0, &Xd, &host);
+    if (st) return st;
+    st = stage_in(h, Z, 1, &Zd, &host);
+    if (st) return st;
+    void* hz = stage_out_ptr(h, HZ, 2, &host);
+    const bool dbl = h->prob.precision == SBEC_FP64;
+    if (riemannian && (host || h->last_grad_X != X)) {
+        st = dbl ? sbec::Ops<double>::grad(h->geom, h->work, Xd, nullptr, nullptr, false, h->stream)
+                 : sbec::Ops<float>::grad(h->geom, h->work, Xd, nullptr, nullptr, false, h->stream);
+        if (st) return st;
+        h->last_grad_X = host ? nullptr : X;
+    }
+    st = dbl ? sbec::Ops<double>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream)
+             : sbec::Ops<float>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream);
+    if (st) return st;
+    if ((st = copy_back(h, HZ, hz))) return st;
+    if (host) st = read_scalars(h);
+    return st;
+}
+
+int sbec_retract(sbec_handle* h, const void* U, const void* Xi, double t, int kind, void* out) {
+    if (!h || !U || !Xi || !out || kind < 1 || kind > 3) return SBEC_ERR_ARG;
+    bool host = false;
+    const void *Ud, *Xd;
+    int st = stage_in(h, U, 0, &Ud, &host);
+    if (st) return st;
+    st = stage_in(h, Xi, 1, &Xd, &host);
+    if (st) return st;
+    void* o = stage_out_ptr(h, out, 2, &host);
+    st = h->prob.precision == SBEC_FP64
+             ? sbec::Ops<double>::retract(h->geom, h->work, Ud, Xd, t, kind, o, h->stream)
+             : sbec::Ops<float>::retract(h->geom, h->work, Ud, Xd, t, kind, o, h->stream);
+    if (st) return st;
+    if ((st = copy_back(h, out, o))) return st;
+    if (host) st = read_scalars(h);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,422 @@
+// Device building blocks of libsbec: complex arithmetic, deterministic block
+// reductions, the shared-memory Stockham FFT used by every pass, and the
+// per-grid-point spin-F terms of the discrete energy (Sec. 3, Eq. 3.7), its
+// gradient (Eq. 3.12) and Hessian-vector product (Eq. 3.13).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sbec {
+
+template <typename T> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+
+template <typename T2> __device__ __forceinline__ T2 mk(decltype(T2::x) a, decltype(T2::x) b) {
+    T2 r; r.x = a; r.y = b; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk<T2>(a.x + b.x, a.y + b.y); }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk<T2>(a.x - b.x, a.y - b.y); }
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    return mk<T2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
+    return mk<T2>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename T2> __device__ __forceinline__ T2 cconj(T2 a) { return mk<T2>(a.x, -a.y); }
+template <typename T2> __device__ __forceinline__ T2 cscale(T2 a, decltype(T2::x) s) { return mk<T2>(a.x * s, a.y * s); }
+template <typename T2> __device__ __forceinline__ decltype(T2::x) cabs2(T2 a) { return a.x * a.x + a.y * a.y; }
+// a += s * b
+template <typename T2> __device__ __forceinline__ void caxpy(T2& a, decltype(T2::x) s, T2 b) { a.x += s * b.x; a.y += s * b.y; }
+// a += b * c (complex)
+template <typename T2> __device__ __forceinline__ void cfma(T2& a, T2 b, T2 c) {
+    a.x += b.x * c.x - b.y * c.y; a.y += b.x * c.y + b.y * c.x;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions.  Each block reduces NQ doubles in a fixed order
+// (warp shuffles, then warp 0 over the per-warp results) and writes them to
+// partials[q * nblk + blk]; reduce_partials sums those in a fixed order too,
+// so every result is bitwise reproducible for a given launch configuration.
+// ---------------------------------------------------------------------------
+template <int NQ>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], double* __restrict__ partials,
+                                                   int nblk, int blk) {
+    __shared__ double red[NQ][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double s = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[q][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double s = lane < nwarp ? red[q][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) partials[(size_t)q * nblk + blk] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Sum of partials[q * nblk + 0 .. nblk-1] by one block, fixed order; result
+// returned to every thread of the block.
+__device__ __forceinline__ double block_sum_partials(const double* __restrict__ partials, int q, int nblk) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += partials[(size_t)q * nblk + i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < nwarp ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Stockham autosort FFT of P pencils of length n = 2^logn held in shared
+// memory: element e of pencil p lives at buf[p * ps + e * es].  Radix-4 stages
+// (sub-transform length Ns = 1, 4, 16, ...) with a radix-2 stage last when
+// logn is odd.  Stage with radix R at length Ns: butterfly j reads elements
+// j + r n/R, multiplies element r by W_{R Ns}^{(j mod Ns) r}, applies the
+// R-point DFT and writes output r to (j - j mod Ns) R + (j mod Ns) + r Ns.
+// The radix-4 stages are in place: every thread holds its ITEMS butterflies in
+// registers across a barrier, so ITEMS * nth >= P n / 4 is required.  The
+// radix-2 stage touches only its own two slots and needs no staging.
+// tw[m] = exp(-2 pi i m / n), m = 0..n-1; INV uses the conjugate twiddles and
+// the conjugate DFT (unnormalised both ways).
+// ---------------------------------------------------------------------------
+template <typename T2, bool INV, int ITEMS>
+__device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, int es,
+                                            const T2* __restrict__ tw, int tid, int nth) {
+    const int n = 1 << logn;
+    int Ns = 1;
+    if (logn >= 2) {
+        const int nb = n >> 2;
+        const int lognb = logn - 2;
+        const int total = P * nb;
+        for (int s = 0; s + 2 <= logn; s += 2) {
+            const int twstep = n / (Ns << 2);
+            T2 v[ITEMS][4];
+            int dst[ITEMS];
+#pragma unroll
+            for (int it = 0; it < ITEMS; ++it) {
+                const int idx = tid + it * nth;
+                if (idx < total) {
+                    const int p = idx >> lognb, j = idx & (nb - 1);
+                    const T2* pb = buf + p * ps;
+                    T2 a0 = pb[j * es], a1 = pb[(j + nb) * es], a2 = pb[(j + 2 * nb) * es],
+                       a3 = pb[(j + 3 * nb) * es];
+                    const int k = j & (Ns - 1);
+                    if (k != 0) {
+                        T2 w1 = tw[k * twstep], w2 = tw[2 * k * twstep], w3 = tw[3 * k * twstep];
+                        if (INV) { w1 = cconj(w1); w2 = cconj(w2); w3 = cconj(w3); }
+                        a1 = cmul(a1, w1); a2 = cmul(a2, w2); a3 = cmul(a3, w3);
+                    }
+                    const T2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+                    const T2 d = csub(a1, a3);
+                    // forward: (a1 - a3) * (-i); inverse: (a1 - a3) * (+i)
+                    const T2 t3 = INV ? mk<T2>(-d.y, d.x) : mk<T2>(d.y, -d.x);
+                    v[it][0] = cadd(t0, t2);
+                    v[it][1] = cadd(t1, t3);
+                    v[it][2] = csub(t0, t2);
+                    v[it][3] = csub(t1, t3);
+                    dst[it] = p * ps + (((j - k) << 2) + k) * es;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < ITEMS; ++it) {
+                const int idx = tid + it * nth;
+                if (idx < total) {
+                    T2* pb = buf + dst[it];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) pb[r * Ns * es] = v[it][r];
+                }
+            }
+            __syncthreads();
+            Ns <<= 2;
+        }
+    }
+    if (logn & 1) {
+        // last stage, Ns = n/2: out[j] = a0 + w a1, out[j + n/2] = a0 - w a1, w = W_n^j
+        const int half = n >> 1;
+        const int total = P * half;
+        for (int idx = tid; idx < total; idx += nth) {
+            const int p = idx >> (logn - 1), j = idx & (half - 1);
+            T2* pb = buf + p * ps;
+            const T2 a0 = pb[j * es];
+            T2 a1 = pb[(j + half) * es];
+            if (j != 0) {
+                T2 w = tw[j];
+                if (INV) w = cconj(w);
+                a1 = cmul(a1, w);
+            }
+            pb[j * es] = cadd(a0, a1);
+            pb[(j + half) * es] = csub(a0, a1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spin-F constants in ladder / pair form (an independent restatement of the
+// Sec. 2 matrices).  Component index i = 0..2F holds l = F - i.
+//   LAD[i]  = sqrt(F(F+1) - (l-1) l) couples i and i+1:  F_+ = sum_i LAD[i] conj(x_i) x_{i+1}
+//             (f_+ raises l-1 -> l; Sec. 2 explicit F_+ of the spin-3 case).
+//   SGL[i]  = (-1)^i / sqrt(2F+1): A00 = sum_i SGL[i] x_i x_{2F-i} (Sec. 2 singlet).
+//   QNT[k][i], k = 0..4 for l = 2, 1, 0, -1, -2 (F = 3): A_{2l} = sum_i QNT[k][i] x_i x_{2F-l-i},
+//             the symmetric matrix entry (A_l)_{i, 2F-l-i} (Sec. 2 quintet; explicit
+//             pair formulas split evenly over the ordered pairs).
+// ---------------------------------------------------------------------------
+template <int F> struct Spin;
+
+template <> struct Spin<1> {
+    static constexpr int C = 3;
+    __device__ static constexpr double lad(int i) { return 1.4142135623730950488; }
+};
+template <> struct Spin<2> {
+    static constexpr int C = 5;
+    __device__ static constexpr double lad(int i) {
+        return (i == 0 || i == 3) ? 2.0 : 2.4494897427831780982;   // 2, sqrt6, sqrt6, 2
+    }
+};
+template <> struct Spin<3> {
+    static constexpr int C = 7;
+    __device__ static constexpr double lad(int i) {
+        return (i == 0 || i == 5) ? 2.4494897427831780982            // sqrt6
+             : (i == 1 || i == 4) ? 3.1622776601683793320            // sqrt10
+                                  : 3.4641016151377545871;           // sqrt12
+    }
+};
+
+__device__ __forceinline__ constexpr double qnt_entry(int k, int i) {
+    // 1/sqrt21 and its multiples
+    constexpr double r21 = 0.21821789023599238127;       // 1/sqrt(21)
+    constexpr double a5 = 2.5 * r21;                     // 5/(2 sqrt21)
+    constexpr double a3 = -1.5 * r21;                    // -3/(2 sqrt21)
+    constexpr double s2 = 1.4142135623730950488 * r21;   // sqrt2/sqrt21
+    constexpr double h2 = 0.5 * s2;                      // sqrt2/(2 sqrt21)
+    constexpr double h15 = -0.5 * 3.8729833462074168852 * r21;  // -sqrt15/(2 sqrt21)
+    constexpr double h10 = 0.5 * 3.1622776601683793320 * r21;   // sqrt10/(2 sqrt21)
+    constexpr double h20 = -0.5 * 4.4721359549995793928 * r21;  // -sqrt20/(2 sqrt21)
+    constexpr double s6 = 2.4494897427831780982 * r21;          // sqrt6/sqrt21
+    switch (k) {
+        case 0:  // l = 2: partner 4 - i
+            return i == 0 ? h10 : i == 1 ? h20 : i == 2 ? s6 : i == 3 ? h20 : i == 4 ? h10 : 0.0;
+        case 1:  // l = 1: partner 5 - i
+            return i == 0 ? a5 : i == 1 ? h15 : i == 2 ? h2 : i == 3 ? h2 : i == 4 ? h15 : i == 5 ? a5 : 0.0;
+        case 2:  // l = 0: partner 6 - i
+            return i == 0 ? a5 : i == 1 ? 0.0 : i == 2 ? a3 : i == 3 ? s2 : i == 4 ? a3 : i == 5 ? 0.0 : a5;
+        case 3:  // l = -1: partner 7 - i
+            return i == 1 ? a5 : i == 2 ? h15 : i == 3 ? h2 : i == 4 ? h2 : i == 5 ? h15 : i == 6 ? a5 : 0.0;
+        default: // l = -2: partner 8 - i
+            return i == 2 ? h10 : i == 3 ? h20 : i == 4 ? s6 : i == 5 ? h20 : i == 6 ? h10 : 0.0;
+    }
+}
+__device__ __forceinline__ constexpr int qnt_l(int k) { return 2 - k; }
+
+// Physical parameters handed to the pointwise code (precomputed on the host).
+struct PointParams {
+    double bz[7];       // Zeeman diagonal b_l = -p l + q l^2 per component index
+    double g0, g1, g2, g3;  // 2 beta_i / dV (gradient / Hessian prefactors)
+    double e0, e1, e2, e3;  // beta_i / (2 dV) (energy prefactors)
+};
+
+// Densities at one grid point (Sec. 3): rho, F_z, F_+, A00, A_{2l}.
+template <int F, typename T2>
+struct Dens {
+    using T = decltype(T2::x);
+    T rho, Fz;
+    T2 Fp, A00, A2[5];
+
+    __device__ __forceinline__ void compute(const T2 (&x)[2 * F + 1]) {
+        constexpr int C = 2 * F + 1;
+        rho = 0; Fz = 0;
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const T a = cabs2(x[i]);
+            rho += a;
+            Fz += T(F - i) * a;
+        }
+        Fp = mk<T2>(0, 0);
+#pragma unroll
+        for (int i = 0; i < C - 1; ++i) {
+            const T2 t = cmulc(x[i], x[i + 1]);
+            caxpy(Fp, T(Spin<F>::lad(i)), t);
+        }
+        A00 = mk<T2>(0, 0);
+        if (F >= 2) {
+            const T sg = T(1.0 / sqrt(double(C)));
+#pragma unroll
+            for (int i = 0; i < F; ++i) caxpy(A00, T((i & 1) ? -2.0 : 2.0) * sg, cmul(x[i], x[C - 1 - i]));
+            caxpy(A00, T((F & 1) ? -1.0 : 1.0) * sg, cmul(x[F], x[F]));
+        }
+        if (F == 3) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int l = qnt_l(k);
+                T2 s = mk<T2>(0, 0);
+#pragma unroll
+                for (int i = 0; i < C; ++i) {
+                    const int ip = 2 * F - l - i;
+                    if (ip >= 0 && ip < C && qnt_entry(k, i) != 0.0) caxpy(s, T(qnt_entry(k, i)), cmul(x[i], x[ip]));
+                }
+                A2[k] = s;
+            }
+        }
+    }
+
+    // interaction + potential + Zeeman energy density (kinetic part excluded)
+    __device__ __forceinline__ double energy_density(const T2 (&x)[2 * F + 1], double V,
+                                                     const PointParams& pp) const {
+        constexpr int C = 2 * F + 1;
+        double e = V * double(rho);
+#pragma unroll
+        for (int i = 0; i < C; ++i) e += pp.bz[i] * double(cabs2(x[i]));
+        double inter = pp.e0 * double(rho) * double(rho) + pp.e1 * (double(Fz) * double(Fz) + double(cabs2(Fp)));
+        if (F >= 2) inter += pp.e2 * double(cabs2(A00));
+        if (F == 3) {
+            double q = 0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) q += double(cabs2(A2[k]));
+            inter += pp.e3 * q;
+        }
+        return e + inter;
+    }
+};
+
+// Gradient (Eq. 3.12) at one grid point, component k, given the Laplacian term lx_k.
+template <int F, typename T2>
+__device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<F, T2>& D, decltype(T2::x) V,
+                                           const PointParams& pp, const T2 (&lx)[2 * F + 1],
+                                           T2 (&g)[2 * F + 1]) {
+    using T = decltype(T2::x);
+    constexpr int C = 2 * F + 1;
+    const T g0 = T(pp.g0), g1 = T(pp.g1), g2 = T(pp.g2), g3 = T(pp.g3);
+    const T2 Fm = cconj(D.Fp);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        T2 r = lx[k];
+        const T lin = T(2) * (V + T(pp.bz[k])) + g0 * D.rho + g1 * T(F - k) * D.Fz;
+        caxpy(r, lin, x[k]);
+        // (g1/2) (F_- (f_+ x)_k + F_+ (f_- x)_k)
+        if (k + 1 < C) cfma(r, cscale(Fm, T(0.5) * g1 * T(Spin<F>::lad(k))), x[k + 1]);
+        if (k >= 1) cfma(r, cscale(D.Fp, T(0.5) * g1 * T(Spin<F>::lad(k - 1))), x[k - 1]);
+        if (F >= 2) {
+            const T sg = T((k & 1) ? -1.0 : 1.0) * T(1.0 / sqrt(double(C)));
+            cfma(r, cscale(D.A00, g2 * sg), cconj(x[C - 1 - k]));
+        }
+        if (F == 3) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int l = qnt_l(q);
+                const int kp = 2 * F - l - k;
+                if (kp >= 0 && kp < C && qnt_entry(q, k) != 0.0)
+                    cfma(r, cscale(D.A2[q], g3 * T(qnt_entry(q, k))), cconj(x[kp]));
+            }
+        }
+        g[k] = r;
+    }
+}
+
+// Hessian-vector product (Eq. 3.13) at one grid point, given lz_k = (L Z)_k.
+template <int F, typename T2>
+__device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&z)[2 * F + 1],
+                                           const Dens<F, T2>& D, decltype(T2::x) V, const PointParams& pp,
+                                           const T2 (&lz)[2 * F + 1], T2 (&hz)[2 * F + 1]) {
+    using T = decltype(T2::x);
+    constexpr int C = 2 * F + 1;
+    const T g0 = T(pp.g0), g1 = T(pp.g1), g2 = T(pp.g2), g3 = T(pp.g3);
+    // directional derivatives of the densities
+    T drho = 0, dFz = 0;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const T re = x[i].x * z[i].x + x[i].y * z[i].y;   // Re(conj(x) z)
+        drho += re;
+        dFz += T(F - i) * re;
+    }
+    drho *= T(2); dFz *= T(2);
+    T2 dFp = mk<T2>(0, 0);
+#pragma unroll
+    for (int i = 0; i < C - 1; ++i) {
+        const T2 t = cadd(cmulc(z[i], x[i + 1]), cmulc(x[i], z[i + 1]));
+        caxpy(dFp, T(Spin<F>::lad(i)), t);
+    }
+    T2 dA00 = mk<T2>(0, 0);
+    if (F >= 2) {
+        const T sg = T(1.0 / sqrt(double(C)));
+#pragma unroll
+        for (int i = 0; i < C; ++i) caxpy(dA00, T((i & 1) ? -2.0 : 2.0) * sg, cmul(z[i], x[C - 1 - i]));
+    }
+    T2 dA2[5];
+    if (F == 3) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int l = qnt_l(q);
+            T2 s = mk<T2>(0, 0);
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const int ip = 2 * F - l - i;
+                if (ip >= 0 && ip < C && qnt_entry(q, i) != 0.0) caxpy(s, T(2.0 * qnt_entry(q, i)), cmul(z[i], x[ip]));
+            }
+            dA2[q] = s;
+        }
+    }
+    const T2 Fm = cconj(D.Fp), dFm = cconj(dFp);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        T2 r = lz[k];
+        const T m = T(F - k);
+        caxpy(r, T(2) * (V + T(pp.bz[k])) + g0 * D.rho + g1 * m * D.Fz, z[k]);
+        caxpy(r, g0 * drho + g1 * m * dFz, x[k]);
+        if (k + 1 < C) {
+            const T c = T(0.5) * g1 * T(Spin<F>::lad(k));
+            cfma(r, cscale(Fm, c), z[k + 1]);
+            cfma(r, cscale(dFm, c), x[k + 1]);
+        }
+        if (k >= 1) {
+            const T c = T(0.5) * g1 * T(Spin<F>::lad(k - 1));
+            cfma(r, cscale(D.Fp, c), z[k - 1]);
+            cfma(r, cscale(dFp, c), x[k - 1]);
+        }
+        if (F >= 2) {
+            const T sg = T((k & 1) ? -1.0 : 1.0) * T(1.0 / sqrt(double(C))) * g2;
+            cfma(r, cscale(D.A00, sg), cconj(z[C - 1 - k]));
+            cfma(r, cscale(dA00, sg), cconj(x[C - 1 - k]));
+        }
+        if (F == 3) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int l = qnt_l(q);
+                const int kp = 2 * F - l - k;
+                if (kp >= 0 && kp < C && qnt_entry(q, k) != 0.0) {
+                    const T c = g3 * T(qnt_entry(q, k));
+                    cfma(r, cscale(D.A2[q], c), cconj(z[kp]));
+                    cfma(r, cscale(dA2[q], c), cconj(x[kp]));
+                }
+            }
+        }
+        hz[k] = r;
+    }
+}
+
+}  // namespace sbec

@@ -1,0 +1,95 @@
+// Host-side internals shared by the C-ABI translation unit and the
+// per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sbec.h"
+
+namespace sbec {
+
+// device scalar-block slots beyond the public SBEC_S_* ones
+enum {
+    S_C2 = 7,          // u^T Gamma^2 u
+    S_PA = 8,          // projection coefficient alpha_w (Lemma 4.1) of the latest projection
+    S_PB = 9,          // projection coefficient beta_w
+    S_NORM2 = 10,      // scratch squared norm
+    S_XFORM = 11,      // reserved
+    S_SIG = 16,        // 7 retraction scales sigma_l (component index order)
+    S_SOLVER = 32,     // solver scalars start here
+    S_COUNT = 128
+};
+
+// Geometry and parameters of one problem as the kernels see it.
+struct Geom {
+    int F, C, dim;
+    int n[3], logn[3];
+    long long G;
+    double dV, invG, M;
+    // device tables
+    const void* tw[3];        // twiddles per axis, T2 (precision of the handle)
+    const double* lam2[3];    // lambda_p^2 per axis in DFT index order
+    const void* V;            // potential, T
+    double bz[7];
+    double g0, g1, g2, g3, e0, e1, e2, e3;
+};
+
+// Kernel identities for the per-kernel launch counter and event timer.
+enum KernelId {
+    K_X_FWD, K_X_FWD_EPW, K_X_INV_GRAD, K_X_INV_HESS, K_X_FULL_GRAD, K_X_FULL_ENERGY, K_X_FULL_HESS,
+    K_S_FWD, K_S_INV, K_S_K2, K_S_PARSEVAL, K_DOT, K_PROJ, K_RETW, K_SCALE, K_FIN, K_RSOLVE, K_TABLES,
+    K_COUNT
+};
+
+// Launch bookkeeping of one handle: every library kernel launch is counted;
+// while enabled, CUDA events are recorded around each launch on its stream so
+// that per-kernel device time can be read back (sbec_profile_read).
+struct Prof {
+    int enabled;
+    long long launches;
+    int nrec, cap;
+    cudaEvent_t* ev;     // 2 * cap events
+    int* kid;            // cap kernel ids
+    double ms[K_COUNT];
+    long long cnt[K_COUNT];
+};
+
+void prof_begin(Prof* p, int kid, cudaStream_t s);
+void prof_end(Prof* p, cudaStream_t s);
+
+struct ProfScope {
+    Prof* p;
+    cudaStream_t s;
+    ProfScope(Prof* p_, int kid, cudaStream_t s_) : p(p_), s(s_) { prof_begin(p, kid, s); }
+    ~ProfScope() { prof_end(p, s); }
+};
+
+struct Work {
+    void* work;        // C*G complex T: FFT intermediate
+    void* work2;       // C*G complex T: projected directions / gradients
+    double* partA;     // per-block partials
+    double* partB;
+    size_t part_cap;   // doubles in each of partA / partB
+    double* scal;      // device scalar block (S_COUNT doubles)
+    int num_sms;
+    Prof* prof;
+};
+
+// per-precision entry points (implemented in sbec_kernels_f64.cu / _f32.cu)
+template <typename T> struct Ops {
+    static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
+    static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
+                    cudaStream_t s);
+    static int hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem,
+                       void* HZ, cudaStream_t s);
+    static int retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind,
+                       void* out, cudaStream_t s);
+    static int init_tables(Geom& g, void* tw_storage, cudaStream_t s);
+    static int harmonic_potential(const Geom& g, void* V, const double* lo, const double* hi, cudaStream_t s);
+    static int convert_potential(const Geom& g, void* V, const double* Vd, cudaStream_t s);
+    static size_t partials_needed(const Geom& g, int num_sms);
+};
+
+}  // namespace sbec

@@ -1,0 +1,943 @@
+// Pass kernels and their orchestration for one precision T (double or float).
+// Included once per precision by sbec_kernels_f64.cu / sbec_kernels_f32.cu.
+//
+// Energy + gradient of a d-dimensional problem (Sec. 3) is d+1 passes over
+// the C-component field, every FFT pencil staged through shared memory:
+//   x pass, forward (all C components of one grid row per block)
+//   strided passes along y (z) forward ... the last axis fused as
+//       forward -> multiply by |k|^2 / G (Eq. 3.5, L = C^* Lambda C) -> inverse
+//   strided inverse passes ... x pass inverse fused with the pointwise
+//       gradient (Eq. 3.12), the energy density (Eq. 3.7) and the per-component
+//       reductions u_l^T u_l, u_l^T g_l that Lemma 4.1 needs.
+// The Hessian-vector product (Eq. 3.13) runs the same passes on Z with a
+// Hessian epilogue; the energy alone needs only forward passes (Parseval).
+#pragma once
+
+#include <math.h>
+
+#include "sbec_device.cuh"
+#include "sbec_internal.h"
+
+namespace sbec {
+
+#define SBEC_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return SBEC_ERR_CUDA;          \
+    } while (0)
+#define SBEC_LAUNCH_CHECK() SBEC_CUDA_TRY(cudaGetLastError())
+
+enum XMode {
+    X_FWD = 0,         // forward x-FFT of every row
+    X_FWD_EPW = 1,     // + pointwise energy partial (q0)
+    X_INV_GRAD = 2,    // inverse x-FFT + gradient epilogue, partials E, n_l, t_l
+    X_INV_HESS = 3,    // inverse x-FFT + Hessian epilogue, partials n_l, t_l
+    X_FULL_GRAD = 4,   // 1D: fwd, |k|^2/G, inv, gradient epilogue
+    X_FULL_ENERGY = 5, // 1D: pointwise energy + fwd + Parseval
+    X_FULL_HESS = 6    // 1D: fwd, |k|^2/G, inv, Hessian epilogue
+};
+
+enum SMode { S_FWD = 0, S_INV = 1, S_K2 = 2, S_PARSEVAL = 3 };
+
+template <int MODE, int C> struct XNQ {
+    static constexpr int v = (MODE == X_INV_GRAD || MODE == X_FULL_GRAD) ? 1 + 2 * C
+                           : (MODE == X_INV_HESS || MODE == X_FULL_HESS) ? 2 * C
+                           : (MODE == X_FULL_ENERGY) ? 2
+                           : (MODE == X_FWD_EPW) ? 1 : 1;
+};
+
+struct XArgs {
+    const void* in;       // field to transform (X, Z or work)
+    void* out;            // destination (work, or the gradient / Hessian output)
+    const void* X;        // state (epilogues)
+    const void* Zd;       // direction (Hessian epilogue, = in for FULL_HESS)
+    const void* V;
+    const void* tw;
+    const double* lam2x;
+    long long G;
+    int logn;             // x length
+    int rpb;              // row groups per block
+    double invG;
+    double sigma;         // Hessian shift
+    const double* scal;   // device scalar block: Lemma 4.2 alpha_g, beta_g (riemannian epilogue)
+    int riem;
+    double* partials;
+    int nblk;
+    PointParams pp;
+};
+
+template <typename T, int F, int MODE, int ITEMS>
+__global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    constexpr int NQ = XNQ<MODE, C>::v;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* buf = reinterpret_cast<T2*>(smem_raw);
+    const int logn = a.logn, n = 1 << logn;
+    const int RPB = a.rpb, P = RPB * C;
+    const long long row0 = (long long)blockIdx.x * RPB;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in);
+    const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
+    const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V);
+
+    for (int idx = tid; idx < P * n; idx += nth) {
+        const int p = idx >> logn, e = idx & (n - 1);
+        const int rg = p / C, c = p - rg * C;
+        buf[idx] = src[(long long)c * a.G + (row0 + rg) * n + e];
+    }
+    __syncthreads();
+
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+
+    if (MODE == X_FWD_EPW || MODE == X_FULL_ENERGY) {
+        for (int idx = tid; idx < RPB * n; idx += nth) {
+            const int rg = idx >> logn, e = idx & (n - 1);
+            T2 x[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) x[c] = buf[(rg * C + c) * n + e];
+            Dens<F, T2> D;
+            D.compute(x);
+            acc[0] += D.energy_density(x, double(Vp[(row0 + rg) * n + e]), a.pp);
+        }
+        __syncthreads();
+    }
+
+    const bool fwd = (MODE == X_FWD || MODE == X_FWD_EPW || MODE >= X_FULL_GRAD);
+    if (fwd) fft_pencils<T2, false, ITEMS>(buf, logn, P, n, 1, tw, tid, nth);
+
+    if (MODE == X_FULL_ENERGY) {
+        // kinetic part by Parseval: (1/(2G)) sum |k|^2 |X^|^2
+        for (int idx = tid; idx < P * n; idx += nth) {
+            const int e = idx & (n - 1);
+            acc[1] += 0.5 * a.invG * a.lam2x[e] * double(cabs2(buf[idx]));
+        }
+    }
+    if (MODE == X_FULL_GRAD || MODE == X_FULL_HESS) {
+        for (int idx = tid; idx < P * n; idx += nth) {
+            const int e = idx & (n - 1);
+            buf[idx] = cscale(buf[idx], T(a.lam2x[e] * a.invG));
+        }
+        __syncthreads();
+    }
+    const bool inv = (MODE == X_INV_GRAD || MODE == X_INV_HESS || MODE == X_FULL_GRAD || MODE == X_FULL_HESS);
+    if (inv) fft_pencils<T2, true, ITEMS>(buf, logn, P, n, 1, tw, tid, nth);
+
+    if (MODE == X_FWD || MODE == X_FWD_EPW) {
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        for (int idx = tid; idx < P * n; idx += nth) {
+            const int p = idx >> logn, e = idx & (n - 1);
+            const int rg = p / C, c = p - rg * C;
+            dst[(long long)c * a.G + (row0 + rg) * n + e] = buf[idx];
+        }
+    }
+
+    if (MODE == X_INV_GRAD || MODE == X_FULL_GRAD) {
+        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X);
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        for (int idx = tid; idx < RPB * n; idx += nth) {
+            const int rg = idx >> logn, e = idx & (n - 1);
+            const long long pt = (row0 + rg) * n + e;
+            T2 x[C], lx[C], g[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                x[c] = Xp[(long long)c * a.G + pt];
+                lx[c] = buf[(rg * C + c) * n + e];
+            }
+            const T V = Vp[pt];
+            Dens<F, T2> D;
+            D.compute(x);
+            grad_point<F, T2>(x, D, V, a.pp, lx, g);
+            double ek = 0.0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) ek += double(x[c].x * lx[c].x + x[c].y * lx[c].y);
+            acc[0] += 0.5 * ek + D.energy_density(x, double(V), a.pp);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                acc[1 + c] += double(cabs2(x[c]));
+                acc[1 + C + c] += double(x[c].x * g[c].x + x[c].y * g[c].y);
+                if (dst) dst[(long long)c * a.G + pt] = g[c];
+            }
+        }
+    }
+
+    if (MODE == X_INV_HESS || MODE == X_FULL_HESS) {
+        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X);
+        const T2* __restrict__ Zp = reinterpret_cast<const T2*>(a.Zd);
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        for (int idx = tid; idx < RPB * n; idx += nth) {
+            const int rg = idx >> logn, e = idx & (n - 1);
+            const long long pt = (row0 + rg) * n + e;
+            T2 x[C], z[C], lz[C], h[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                x[c] = Xp[(long long)c * a.G + pt];
+                z[c] = Zp[(long long)c * a.G + pt];
+                lz[c] = buf[(rg * C + c) * n + e];
+            }
+            const T V = Vp[pt];
+            Dens<F, T2> D;
+            D.compute(x);
+            hess_point<F, T2>(x, z, D, V, a.pp, lz, h);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                T s = T(a.sigma);
+                if (a.riem) s -= T(a.scal[SBEC_S_ALPHA_G] + a.scal[SBEC_S_BETA_G] * double(F - c));
+                caxpy(h[c], s, z[c]);
+                acc[c] += double(cabs2(x[c]));
+                acc[C + c] += double(x[c].x * h[c].x + x[c].y * h[c].y);
+                dst[(long long)c * a.G + pt] = h[c];
+            }
+        }
+    }
+
+    if (MODE != X_FWD) block_reduce_store<NQ>(acc, a.partials, a.nblk, blockIdx.x);
+}
+
+struct SArgs {
+    const void* in;
+    void* out;
+    const void* tw;
+    const double* lam2[3];
+    long long G;
+    int axis;         // 1 = y, 2 = z
+    int logn;         // axis length
+    int W;            // pencils (consecutive x) per block
+    int nx, ny, nz;
+    int ntx;          // nx / W
+    int nouter;       // nz for axis y, ny for axis z
+    long long estride;
+    double invG;
+    double* partials;
+    int nblk;
+};
+
+template <typename T, int MODE, int ITEMS>
+__global__ void __launch_bounds__(512) k_spass(const SArgs a) {
+    using T2 = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* buf = reinterpret_cast<T2*>(smem_raw);
+    const int logn = a.logn, n = 1 << logn, W = a.W;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    long long b = blockIdx.x;
+    const int xt = (int)(b % a.ntx); b /= a.ntx;
+    const int o = (int)(b % a.nouter);
+    const int c = (int)(b / a.nouter);
+    const long long obase = (a.axis == 1) ? (long long)o * a.ny * a.nx : (long long)o * a.nx;
+    const long long base = (long long)c * a.G + obase + (long long)xt * W;
+    const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in);
+    const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
+
+    for (int idx = tid; idx < W * n; idx += nth) {
+        const int e = idx / W, w = idx - e * W;
+        buf[idx] = src[base + e * a.estride + w];
+    }
+    __syncthreads();
+    fft_pencils<T2, MODE == S_INV, ITEMS>(buf, logn, W, 1, W, tw, tid, nth);
+
+    if (MODE == S_K2 || MODE == S_PARSEVAL) {
+        double acc[1] = {0.0};
+        for (int idx = tid; idx < W * n; idx += nth) {
+            const int e = idx / W, w = idx - e * W;
+            // frequency indices: x and the pass axis from the tile, the third axis from o
+            const int ix = xt * W + w;
+            const int iy = (a.axis == 1) ? e : o;
+            const int iz = (a.axis == 2) ? e : o;
+            const double k2 = a.lam2[0][ix] + a.lam2[1][iy] + a.lam2[2][iz];
+            if (MODE == S_K2) {
+                buf[idx] = cscale(buf[idx], T(k2 * a.invG));
+            } else {
+                acc[0] += 0.5 * a.invG * k2 * double(cabs2(buf[idx]));
+            }
+        }
+        if (MODE == S_PARSEVAL) {
+            block_reduce_store<1>(acc, a.partials, a.nblk, blockIdx.x);
+            return;
+        }
+        __syncthreads();
+        fft_pencils<T2, true, ITEMS>(buf, logn, W, 1, W, tw, tid, nth);
+    }
+    T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+    for (int idx = tid; idx < W * n; idx += nth) {
+        const int e = idx / W, w = idx - e * W;
+        dst[base + e * a.estride + w] = buf[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels over grid points (grid-stride), all C components per point.
+// ---------------------------------------------------------------------------
+
+// partials: n_l = |u_l|^2 (q = l index), t_l = <u_l, w_l> (q = C + l)
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials,
+                                                    int nblk) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
+    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp);
+    double acc[2 * C];
+#pragma unroll
+    for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const T2 u = U[c * G + p], w = Wv[c * G + p];
+            acc[c] += double(cabs2(u));
+            acc[C + c] += double(u.x * w.x + u.y * w.y);
+        }
+    }
+    block_reduce_store<2 * C>(acc, partials, nblk, blockIdx.x);
+}
+
+// out_l = W_l - (alpha + beta l) U_l with (alpha, beta) = scal[ia], scal[ib]; partial |out|^2
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* Wp, void* Op, long long G,
+                                                    const double* __restrict__ scal, int ia, int ib,
+                                                    double* partials, int nblk) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
+    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp);
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    T coef[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) coef[c] = T(scal[ia] + scal[ib] * double(F - c));
+    double acc[1] = {0.0};
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const T2 u = U[c * G + p];
+            T2 w = Wv[c * G + p];
+            caxpy(w, -coef[c], u);
+            acc[0] += double(cabs2(w));
+            if (O) O[c * G + p] = w;
+        }
+    }
+    block_reduce_store<1>(acc, partials, nblk, blockIdx.x);
+}
+
+// w = U + t Xi into out; partials m_l = |w_l|^2
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
+                                                   double* partials, int nblk) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
+    const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp);
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    double acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    const T tt = T(t);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            T2 w = U[c * G + p];
+            caxpy(w, tt, Xi[c * G + p]);
+            acc[c] += double(cabs2(w));
+            O[c * G + p] = w;
+        }
+    }
+    block_reduce_store<C>(acc, partials, nblk, blockIdx.x);
+}
+
+// out_l *= scal[S_SIG + l]
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    T s[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) s[c] = T(scal[S_SIG + c]);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) O[c * G + p] = cscale(O[c * G + p], s[c]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finalize kernels (one block of 256 threads): fixed-order sums of the
+// partials and the scalar algebra of Lemma 4.1 / 4.2 and of the retractions.
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void set_status(double* scal, int code) {
+    if (scal[SBEC_S_STATUS] == 0.0) scal[SBEC_S_STATUS] = double(code);
+}
+
+// energy: scal[E] = sum(partA q0) + sum(partB q0)   (1D: partA q0 + partA q1)
+static __global__ void k_fin_energy(const double* pa, int na, int nqa, const double* pb, int nb, double* scal) {
+    double e = 0.0;
+    for (int q = 0; q < nqa; ++q) e += block_sum_partials(pa, q, na);
+    if (pb) e += block_sum_partials(pb, 0, nb);
+    if (threadIdx.x == 0) {
+        scal[SBEC_S_ENERGY] = e;
+        if (!isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
+    }
+}
+
+// gradient / projection coefficients (Lemma 4.1, Eq. ab) from n_l (q = qn + l) and
+// t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
+// beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
+static __global__ void k_fin_proj(const double* pa, int na, int F, int qe, int qn, int qt, double M, double* scal,
+                           int slot_a, int slot_b, int write_grad_info) {
+    const int C = 2 * F + 1;
+    double e = 0.0, a = 0.0, b = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
+    if (qe >= 0) e = block_sum_partials(pa, qe, na);
+    for (int i = 0; i < C; ++i) {
+        const double l = double(F - i);
+        const double nl = block_sum_partials(pa, qn + i, na);
+        const double tl = block_sum_partials(pa, qt + i, na);
+        a += nl; b += l * nl; c += l * l * nl;
+        ug += tl; uGg += l * tl;
+    }
+    if (threadIdx.x == 0) {
+        const double au = c - M * M;
+        const double al = (c * ug - M * uGg) / au;
+        const double be = (uGg - M * ug) / au;
+        if (!isfinite(c) || !isfinite(ug) || !isfinite(uGg) || !isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
+        if (!(au > 0.0)) set_status(scal, SBEC_ERR_DOMAIN);
+        scal[slot_a] = al;
+        scal[slot_b] = be;
+        if (write_grad_info) {
+            scal[SBEC_S_ENERGY] = e;
+            scal[SBEC_S_MASS] = a;
+            scal[SBEC_S_MAG] = b;
+            scal[S_C2] = c;
+            if (!isfinite(e) || !isfinite(al) || !isfinite(be)) set_status(scal, SBEC_ERR_NONFINITE);
+        }
+    }
+}
+
+static __global__ void k_fin_norm(const double* pa, int na, double* scal, int slot) {
+    const double s = block_sum_partials(pa, 0, na);
+    if (threadIdx.x == 0) {
+        scal[slot] = s;
+        if (!isfinite(s)) set_status(scal, SBEC_ERR_NONFINITE);
+    }
+}
+
+// Retraction scales sigma_l from m_l = |w_l|^2 (Sec. 6).  kind 1: Lemma 5.1 (r is
+// the zero of the increasing h1 on (1/(f1-M), 1/(f2-M)): bisection, then Newton);
+// kind 2: Lemma 5.3 (r the positive zero of h3 = h2 t^{-f1-F}: doubling bracket,
+// bisection, Newton); kind 3: Lemma 5.4 closed form.
+static __global__ void k_retract_solve(const double* pa, int na, int F, double M, int kind, double* scal) {
+    __shared__ double m[7];
+    const int C = 2 * F + 1;
+    for (int i = 0; i < C; ++i) {
+        const double v = block_sum_partials(pa, i, na);
+        if (threadIdx.x == 0) m[i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double sig[7];
+    for (int i = 0; i < 7; ++i) sig[i] = 0.0;
+    // f1 = min l with w_l != 0, f2 = max
+    int i1 = -1, i2 = -1;  // component indices of f2 (smallest index) and f1 (largest index)
+    for (int i = 0; i < C; ++i)
+        if (m[i] > 0.0) { if (i1 < 0) i1 = i; i2 = i; }
+    bool ok = (i1 >= 0);
+    const double f2 = ok ? double(F - i1) : 0.0, f1 = ok ? double(F - i2) : 0.0;
+    if (kind == 3) {
+        double a = 0, b = 0, c = 0;
+        for (int i = 0; i < C; ++i) { const double l = double(F - i); a += m[i]; b += l * m[i]; c += l * l * m[i]; }
+        const double den = a * c - b * b;
+        for (int i = 0; i < C && ok; ++i) {
+            const double l = double(F - i);
+            const double num = c - (M + l) * b + M * l * a;
+            if (!(num > 0.0 && den > 0.0)) ok = false; else sig[i] = sqrt(num / den);
+        }
+    } else if (ok && f1 < M && M < f2) {
+        if (kind == 1) {
+            double lo = 1.0 / (f1 - M), hi = 1.0 / (f2 - M);
+            const double lo0 = lo, hi0 = hi;
+            for (int it = 0; it < 400; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (!(mid > lo && mid < hi)) break;
+                double h1 = 0.0;
+                for (int i = i1; i <= i2; ++i) {
+                    const double d = double(F - i) - M, q = 1.0 - d * mid;
+                    h1 += d * m[i] / (q * q);
+                }
+                if (h1 < 0.0) lo = mid; else hi = mid;
+            }
+            double r = 0.5 * (lo + hi);
+            for (int it = 0; it < 3; ++it) {
+                double h1 = 0.0, dh = 0.0;
+                for (int i = i1; i <= i2; ++i) {
+                    const double d = double(F - i) - M, q = 1.0 - d * r;
+                    h1 += d * m[i] / (q * q);
+                    dh += 2.0 * d * d * m[i] / (q * q * q);
+                }
+                if (dh > 0.0) {
+                    const double rn = r - h1 / dh;
+                    if (rn > lo0 && rn < hi0) r = rn;
+                }
+            }
+            double s = 0.0;
+            for (int i = i1; i <= i2; ++i) {
+                const double q = 1.0 - (double(F - i) - M) * r;
+                s += m[i] / (q * q);
+            }
+            for (int i = i1; i <= i2; ++i) sig[i] = 1.0 / (sqrt(s) * (1.0 - (double(F - i) - M) * r));
+        } else {
+            // h3(t) = sum_{j} (j + f1 - M) m_{f1 + j} t^j, component of l = f1 + j is F - f1 - j
+            auto h3 = [&](double t, double* dh) {
+                double v = 0.0, dv = 0.0, tp = 1.0, tpm = 0.0;
+                const int jmax = int(f2 - f1);
+                for (int j = 0; j <= jmax; ++j) {
+                    const int i = F - int(f1) - j;
+                    const double cf = (double(j) + f1 - M) * m[i];
+                    v += cf * tp;
+                    dv += double(j) * cf * tpm;
+                    tpm = tp;
+                    tp *= t;
+                }
+                if (dh) *dh = dv;
+                return v;
+            };
+            double lo = 0.0, hi = 1.0;
+            int guard = 0;
+            while (h3(hi, nullptr) <= 0.0 && guard < 2000) { lo = hi; hi *= 2.0; ++guard; }
+            if (guard >= 2000) ok = false;
+            for (int it = 0; it < 2000 && ok; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (!(mid > lo && mid < hi)) break;
+                if (h3(mid, nullptr) < 0.0) lo = mid; else hi = mid;
+            }
+            double r = 0.5 * (lo + hi);
+            for (int it = 0; it < 3 && ok; ++it) {
+                double dh;
+                const double v = h3(r, &dh);
+                if (dh > 0.0) { const double rn = r - v / dh; if (rn > 0.0) r = rn; }
+            }
+            double ssum = 0.0;
+            for (int i = 0; i < C; ++i) ssum += m[i] * pow(r, double(F - i));
+            const double s0 = sqrt(1.0 / ssum);
+            for (int i = 0; i < C; ++i) sig[i] = s0 * pow(r, 0.5 * double(F - i));
+        }
+    } else {
+        ok = false;
+    }
+    for (int i = 0; i < 7; ++i) {
+        if (!isfinite(sig[i])) ok = false;
+        scal[S_SIG + i] = sig[i];
+    }
+    if (!ok) set_status(scal, SBEC_ERR_DOMAIN);
+}
+
+// ---------------------------------------------------------------------------
+// Tables
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_twiddles(void* twp, int n) {
+    using T2 = typename C2<T>::t;
+    T2* tw = reinterpret_cast<T2*>(twp);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * double(m) / double(n), &s, &c);
+        tw[m] = mk<T2>(T(c), T(s));
+    }
+}
+
+template <typename T>
+__global__ void k_harmonic(void* Vp, int nx, int ny, int nz, double x0, double hx, double y0, double hy, double z0,
+                           double hz, int dim) {
+    T* V = reinterpret_cast<T*>(Vp);
+    const long long G = (long long)nx * ny * nz;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+        const int ix = int(p % nx), iy = int((p / nx) % ny), iz = int(p / ((long long)nx * ny));
+        const double x = x0 + hx * ix, y = y0 + hy * iy, z = z0 + hz * iz;
+        double v = x * x;
+        if (dim >= 2) v += y * y;
+        if (dim >= 3) v += z * z;
+        V[p] = T(0.5 * v);
+    }
+}
+
+template <typename T>
+__global__ void k_convert(void* Vp, const double* Vd, long long G) {
+    T* V = reinterpret_cast<T*>(Vp);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x)
+        V[p] = T(Vd[p]);
+}
+
+// ---------------------------------------------------------------------------
+// Launch configuration
+// ---------------------------------------------------------------------------
+struct XCfg { int rpb, nth, items, nblk; size_t smem; };
+struct SCfg { int W, nth, items, nblk; size_t smem; };
+
+template <typename T>
+static XCfg xcfg(const Geom& g) {
+    using T2 = typename C2<T>::t;
+    const int n = g.n[0];
+    const long long rows = g.G / n;
+    int rpb = 1;
+    while ((long long)rpb * 2 * g.C * n <= 2048 && rows % (rpb * 2) == 0) rpb *= 2;
+    const int P = rpb * g.C;
+    const int bfly = (n >= 4) ? P * n / 4 : P;
+    int nth = ((bfly + 31) / 32) * 32;
+    if (nth > 512) nth = 512;
+    if (nth < 64) nth = 64;
+    int items = (bfly + nth - 1) / nth;
+    int it2 = 1;
+    while (it2 < items) it2 *= 2;
+    XCfg c;
+    c.rpb = rpb; c.nth = nth; c.items = it2; c.nblk = (int)(rows / rpb);
+    c.smem = (size_t)P * n * sizeof(T2);
+    return c;
+}
+
+template <typename T>
+static SCfg scfg(const Geom& g, int axis, int num_sms) {
+    using T2 = typename C2<T>::t;
+    const int n = g.n[axis];
+    const int nx = g.n[0];
+    const long long outer = (axis == 1) ? g.n[2] : g.n[1];
+    int W = (sizeof(T) == 8) ? 8 : 16;
+    if (W > nx) W = nx;
+    // prefer at least 4 blocks per SM when the grid is small
+    while (W > 2 && (long long)g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
+    const int bfly = (n >= 4) ? W * n / 4 : W;
+    int nth = ((bfly + 31) / 32) * 32;
+    if (nth > 512) nth = 512;
+    if (nth < 64) nth = 64;
+    int items = (bfly + nth - 1) / nth;
+    int it2 = 1;
+    while (it2 < items) it2 *= 2;
+    SCfg c;
+    c.W = W; c.nth = nth; c.items = it2;
+    c.nblk = (int)((long long)g.C * outer * (nx / W));
+    c.smem = (size_t)W * n * sizeof(T2);
+    return c;
+}
+
+static int elem_blocks(long long G, int num_sms) {
+    long long b = (G + 255) / 256;
+    const long long cap = 8LL * num_sms;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+static PointParams point_params(const Geom& g) {
+    PointParams pp;
+    for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
+    pp.g0 = g.g0; pp.g1 = g.g1; pp.g2 = g.g2; pp.g3 = g.g3;
+    pp.e0 = g.e0; pp.e1 = g.e1; pp.e2 = g.e2; pp.e3 = g.e3;
+    return pp;
+}
+
+// Dynamic shared memory above the default carve-out needs an opt-in per kernel;
+// the static shared memory of the reductions comes on top, so opt in above
+// 32 KB.  `granted` is the caller's per-kernel record of the size already set.
+template <typename K>
+static int ensure_smem(K kern, size_t bytes, size_t& granted) {
+    if (bytes > 32 * 1024 && bytes > granted) {
+        SBEC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        granted = bytes;
+    }
+    return SBEC_OK;
+}
+
+template <int MODE> struct XKid {
+    static constexpr int v = MODE == X_FWD ? K_X_FWD : MODE == X_FWD_EPW ? K_X_FWD_EPW
+                           : MODE == X_INV_GRAD ? K_X_INV_GRAD : MODE == X_INV_HESS ? K_X_INV_HESS
+                           : MODE == X_FULL_GRAD ? K_X_FULL_GRAD : MODE == X_FULL_ENERGY ? K_X_FULL_ENERGY
+                           : K_X_FULL_HESS;
+};
+template <int MODE> struct SKid {
+    static constexpr int v = MODE == S_FWD ? K_S_FWD : MODE == S_INV ? K_S_INV : MODE == S_K2 ? K_S_K2 : K_S_PARSEVAL;
+};
+
+template <typename T, int F, int MODE, int ITEMS>
+static int launch_x_items(const XCfg& c, const XArgs& a, const Work& w, cudaStream_t s) {
+    auto kern = k_xpass<T, F, MODE, ITEMS>;
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, c.smem, granted)) return st;
+    ProfScope ps(w.prof, XKid<MODE>::v, s);
+    kern<<<c.nblk, c.nth, c.smem, s>>>(a);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
+template <typename T, int F, int MODE>
+static int launch_x(const XCfg& c, const XArgs& a, const Work& w, cudaStream_t s) {
+    switch (c.items) {
+        case 1: return launch_x_items<T, F, MODE, 1>(c, a, w, s);
+        case 2: return launch_x_items<T, F, MODE, 2>(c, a, w, s);
+        case 4: return launch_x_items<T, F, MODE, 4>(c, a, w, s);
+        case 8: return launch_x_items<T, F, MODE, 8>(c, a, w, s);
+        default: return SBEC_ERR_ARG;
+    }
+}
+
+template <typename T, int MODE, int ITEMS>
+static int launch_s_items(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
+    auto kern = k_spass<T, MODE, ITEMS>;
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, c.smem, granted)) return st;
+    ProfScope ps(w.prof, SKid<MODE>::v, s);
+    kern<<<c.nblk, c.nth, c.smem, s>>>(a);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
+template <typename T, int MODE>
+static int launch_s(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
+    switch (c.items) {
+        case 1: return launch_s_items<T, MODE, 1>(c, a, w, s);
+        case 2: return launch_s_items<T, MODE, 2>(c, a, w, s);
+        case 4: return launch_s_items<T, MODE, 4>(c, a, w, s);
+        case 8: return launch_s_items<T, MODE, 8>(c, a, w, s);
+        default: return SBEC_ERR_ARG;
+    }
+}
+
+// launch of an elementwise / finalize kernel with bookkeeping
+#define SBEC_LAUNCH(kid, kern, grid, block, ...)            \
+    do {                                                    \
+        ProfScope ps_(w.prof, kid, s);                      \
+        kern<<<grid, block, 0, s>>>(__VA_ARGS__);           \
+        SBEC_LAUNCH_CHECK();                                \
+    } while (0)
+
+template <typename T>
+static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void* out, double* part) {
+    SArgs a;
+    a.in = in; a.out = out; a.tw = g.tw[axis];
+    for (int i = 0; i < 3; ++i) a.lam2[i] = g.lam2[i];
+    a.G = g.G; a.axis = axis; a.logn = g.logn[axis]; a.W = c.W;
+    a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
+    a.ntx = g.n[0] / c.W;
+    a.nouter = (axis == 1) ? g.n[2] : g.n[1];
+    a.estride = (axis == 1) ? (long long)g.n[0] : (long long)g.n[0] * g.n[1];
+    a.invG = g.invG;
+    a.partials = part; a.nblk = c.nblk;
+    return a;
+}
+
+template <typename T>
+static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, double* part) {
+    XArgs a;
+    a.in = in; a.out = out; a.X = nullptr; a.Zd = nullptr; a.V = g.V; a.tw = g.tw[0];
+    a.lam2x = g.lam2[0]; a.G = g.G; a.logn = g.logn[0]; a.rpb = c.rpb; a.invG = g.invG;
+    a.sigma = 0.0; a.scal = nullptr; a.riem = 0;
+    a.partials = part; a.nblk = c.nblk;
+    a.pp = point_params(g);
+    return a;
+}
+
+// Forward transforms of every axis but x after the x pass, then the fused
+// k-space pass on the last axis, then the inverse passes back to (but not
+// including) x.  in = out = w.work on entry (x pass already done).
+template <typename T>
+static int middle_passes(const Geom& g, const Work& w, cudaStream_t s) {
+    const int d = g.dim;
+    if (d == 2) {
+        const SCfg c = scfg<T>(g, 1, w.num_sms);
+        return launch_s<T, S_K2>(c, sargs<T>(g, c, 1, w.work, w.work, nullptr), w, s);
+    }
+    // d == 3
+    const SCfg cy = scfg<T>(g, 1, w.num_sms), cz = scfg<T>(g, 2, w.num_sms);
+    int st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+    if (st) return st;
+    st = launch_s<T, S_K2>(cz, sargs<T>(g, cz, 2, w.work, w.work, nullptr), w, s);
+    if (st) return st;
+    return launch_s<T, S_INV>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+}
+
+template <typename T, int F>
+static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
+                  cudaStream_t s) {
+    constexpr int C = 2 * F + 1;
+    const XCfg c = xcfg<T>(g);
+    if ((size_t)c.nblk * (1 + 2 * C) > w.part_cap) return SBEC_ERR_ARG;
+    void* gout = Geuc ? Geuc : ((Griem || want_norm) ? w.work2 : nullptr);
+    int st;
+    if (g.dim == 1) {
+        XArgs a = xargs<T>(g, c, X, gout, w.partA);
+        a.X = X;
+        st = launch_x<T, F, X_FULL_GRAD>(c, a, w, s);
+        if (st) return st;
+    } else {
+        st = launch_x<T, F, X_FWD>(c, xargs<T>(g, c, X, w.work, nullptr), w, s);
+        if (st) return st;
+        st = middle_passes<T>(g, w, s);
+        if (st) return st;
+        XArgs a = xargs<T>(g, c, w.work, gout, w.partA);
+        a.X = X;
+        st = launch_x<T, F, X_INV_GRAD>(c, a, w, s);
+        if (st) return st;
+    }
+    SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partA, c.nblk, F, 0, 1, 1 + C, g.M, w.scal, SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+    if (Griem || want_norm) {
+        const int nb = elem_blocks(g.G, w.num_sms);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G, SBEC_S_BETA_G, w.partB, nb);
+        SBEC_LAUNCH(K_FIN, k_fin_norm, 1, 256, w.partB, nb, w.scal, SBEC_S_RGRAD_NORM2);
+    }
+    return SBEC_OK;
+}
+
+template <typename T, int F>
+static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s) {
+    const XCfg c = xcfg<T>(g);
+    int st;
+    if (g.dim == 1) {
+        st = launch_x<T, F, X_FULL_ENERGY>(c, xargs<T>(g, c, X, nullptr, w.partA), w, s);
+        if (st) return st;
+        SBEC_LAUNCH(K_FIN, k_fin_energy, 1, 256, w.partA, c.nblk, 2, nullptr, 0, w.scal);
+        return SBEC_OK;
+    }
+    st = launch_x<T, F, X_FWD_EPW>(c, xargs<T>(g, c, X, w.work, w.partA), w, s);
+    if (st) return st;
+    int nbB;
+    if (g.dim == 2) {
+        const SCfg cy = scfg<T>(g, 1, w.num_sms);
+        st = launch_s<T, S_PARSEVAL>(cy, sargs<T>(g, cy, 1, w.work, nullptr, w.partB), w, s);
+        nbB = cy.nblk;
+    } else {
+        const SCfg cy = scfg<T>(g, 1, w.num_sms), cz = scfg<T>(g, 2, w.num_sms);
+        st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+        if (st) return st;
+        st = launch_s<T, S_PARSEVAL>(cz, sargs<T>(g, cz, 2, w.work, nullptr, w.partB), w, s);
+        nbB = cz.nblk;
+    }
+    if (st) return st;
+    SBEC_LAUNCH(K_FIN, k_fin_energy, 1, 256, w.partA, c.nblk, 1, w.partB, nbB, w.scal);
+    return SBEC_OK;
+}
+
+template <typename T, int F>
+static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
+                  cudaStream_t s) {
+    constexpr int C = 2 * F + 1;
+    const int nb = elem_blocks(g.G, w.num_sms);
+    const void* zin = Z;
+    if (riem) {
+        // xi = P_u Z (Lemma 4.1)
+        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), nb, 256, X, Z, g.G, w.partB, nb);
+        SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partB, nb, F, -1, 0, C, g.M, w.scal, S_PA, S_PB, 0);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB, w.partB, nb);
+        zin = w.work2;
+    }
+    const XCfg c = xcfg<T>(g);
+    // the Lemma 4.2 coefficients alpha_g, beta_g are read by the epilogue from the
+    // scalar block written by the latest gradient at X
+    int st;
+    if (g.dim == 1) {
+        XArgs a = xargs<T>(g, c, zin, HZ, w.partA);
+        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal;
+        st = launch_x<T, F, X_FULL_HESS>(c, a, w, s);
+        if (st) return st;
+    } else {
+        st = launch_x<T, F, X_FWD>(c, xargs<T>(g, c, zin, w.work, nullptr), w, s);
+        if (st) return st;
+        st = middle_passes<T>(g, w, s);
+        if (st) return st;
+        XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
+        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal;
+        st = launch_x<T, F, X_INV_HESS>(c, a, w, s);
+        if (st) return st;
+    }
+    if (riem) {
+        SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partA, c.nblk, F, -1, 0, C, g.M, w.scal, S_PA, S_PB, 0);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB, nb);
+    }
+    return SBEC_OK;
+}
+
+template <typename T, int F>
+static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
+                     cudaStream_t s) {
+    const int nb = elem_blocks(g.G, w.num_sms);
+    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), nb, 256, U, Xi, t, out, g.G, w.partB, nb);
+    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, 1, 256, w.partB, nb, F, g.M, kind, w.scal);
+    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), nb, 256, out, g.G, w.scal);
+    return SBEC_OK;
+}
+
+#define SBEC_DISPATCH_F(expr_tmpl)                 \
+    switch (g.F) {                                 \
+        case 1: return expr_tmpl(1);               \
+        case 2: return expr_tmpl(2);               \
+        case 3: return expr_tmpl(3);               \
+        default: return SBEC_ERR_ARG;              \
+    }
+
+template <typename T>
+int Ops<T>::energy(const Geom& g, const Work& w, const void* X, cudaStream_t s) {
+#define E_(F) energy_F<T, F>(g, w, X, s)
+    SBEC_DISPATCH_F(E_)
+#undef E_
+}
+
+template <typename T>
+int Ops<T>::grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
+                 cudaStream_t s) {
+#define G_(F) grad_F<T, F>(g, w, X, Geuc, Griem, want_norm, s)
+    SBEC_DISPATCH_F(G_)
+#undef G_
+}
+
+template <typename T>
+int Ops<T>::hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
+                    cudaStream_t s) {
+#define H_(F) hess_F<T, F>(g, w, X, Z, sigma, riem, HZ, s)
+    SBEC_DISPATCH_F(H_)
+#undef H_
+}
+
+template <typename T>
+int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
+                    cudaStream_t s) {
+#define R_(F) retract_F<T, F>(g, w, U, Xi, t, kind, out, s)
+    SBEC_DISPATCH_F(R_)
+#undef R_
+}
+
+template <typename T>
+int Ops<T>::init_tables(Geom& g, void* tw_storage, cudaStream_t s) {
+    using T2 = typename C2<T>::t;
+    T2* base = reinterpret_cast<T2*>(tw_storage);
+    size_t off = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int n = g.n[ax];
+        g.tw[ax] = base + off;
+        k_twiddles<T><<<(n + 255) / 256, 256, 0, s>>>(base + off, n);
+        SBEC_LAUNCH_CHECK();
+        off += n;
+    }
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::harmonic_potential(const Geom& g, void* V, const double* lo, const double* hi, cudaStream_t s) {
+    const double hx = (hi[0] - lo[0]) / g.n[0], hy = (hi[1] - lo[1]) / g.n[1], hz = (hi[2] - lo[2]) / g.n[2];
+    k_harmonic<T><<<1024, 256, 0, s>>>(V, g.n[0], g.n[1], g.n[2], lo[0], hx, lo[1], hy, lo[2], hz, g.dim);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::convert_potential(const Geom& g, void* V, const double* Vd, cudaStream_t s) {
+    k_convert<T><<<1024, 256, 0, s>>>(V, Vd, g.G);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
+template <typename T>
+size_t Ops<T>::partials_needed(const Geom& g, int num_sms) {
+    const XCfg c = xcfg<T>(g);
+    size_t need = (size_t)c.nblk * (1 + 2 * g.C);
+    const size_t e = (size_t)elem_blocks(g.G, num_sms) * (2 * g.C);
+    if (e > need) need = e;
+    for (int ax = 1; ax < g.dim; ++ax) {
+        const SCfg sc = scfg<T>(g, ax, num_sms);
+        if ((size_t)sc.nblk > need) need = sc.nblk;
+    }
+    return need;
+}
+
+}  // namespace sbec

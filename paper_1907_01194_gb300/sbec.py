@@ -1,0 +1,206 @@
+"""Python binding of libsbec (argument marshalling only).
+
+Every computation runs in the compiled CUDA library; this module converts
+arguments (torch tensors on the GPU, or numpy arrays on the host) to plain
+pointers and sizes and forwards the call through the C ABI declared in
+include/sbec.h.  Importing it loads the library and raises ImportError if it
+has not been built; there is no fallback implementation.
+
+Arrays use the library's layout: complex tensors of shape (C, n_z, n_y, n_x)
+(1D: (C, n_x), 2D: (C, n_y, n_x)), components l = F..-F, holding the paper's
+scaled variable X = sqrt(dV) phi; complex128 for precision "fp64", complex64
+for "mixed".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("SBEC_LIB", os.path.join(_HERE, "libsbec.so"))
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsbec is not built ({LIB_PATH} missing): run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_DOMAIN, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOCONV = range(7)
+FP64, MIXED = 0, 1
+S_ENERGY, S_RGRAD_NORM2, S_ALPHA_G, S_BETA_G, S_MASS, S_MAG, S_STATUS = range(7)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_int), ("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("beta", ctypes.c_double * 4), ("p", ctypes.c_double), ("q", ctypes.c_double),
+                ("M", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+_vp, _dp, _int, _dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+_lib.sbec_create.argtypes = [ctypes.POINTER(Problem), _vp, _vp, ctypes.POINTER(_vp)]
+_lib.sbec_destroy.argtypes = [_vp]
+_lib.sbec_energy.argtypes = [_vp, _vp, _dp]
+_lib.sbec_grad.argtypes = [_vp, _vp, _vp, _vp, _dp, _dp]
+_lib.sbec_hessvec.argtypes = [_vp, _vp, _vp, _dbl, _int, _vp]
+_lib.sbec_retract.argtypes = [_vp, _vp, _vp, _dbl, _int, _vp]
+_lib.sbec_sync.argtypes = [_vp]
+_lib.sbec_scalars.argtypes = [_vp]
+_lib.sbec_scalars.restype = _vp
+_lib.sbec_launch_count.argtypes = [_vp]
+_lib.sbec_launch_count.restype = ctypes.c_longlong
+_lib.sbec_profile.argtypes = [_vp, _int]
+_lib.sbec_profile_read.argtypes = [_vp, _int, ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(_int)]
+_lib.sbec_status_string.argtypes = [_int]
+_lib.sbec_status_string.restype = ctypes.c_char_p
+for _f in ("sbec_create", "sbec_destroy", "sbec_energy", "sbec_grad", "sbec_hessvec",
+           "sbec_retract", "sbec_sync", "sbec_profile", "sbec_profile_read"):
+    getattr(_lib, _f).restype = _int
+
+EXPORTED = ("sbec_create", "sbec_destroy", "sbec_energy", "sbec_grad", "sbec_hessvec",
+            "sbec_retract", "sbec_sync", "sbec_scalars", "sbec_status_string",
+            "sbec_launch_count", "sbec_profile", "sbec_profile_read")
+
+
+class SbecError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib.sbec_status_string(status).decode()} (status {status})")
+
+
+def _check(status, where):
+    if status != OK:
+        raise SbecError(status, where)
+
+
+def _ptr(a):
+    """Plain pointer of a contiguous torch tensor (device or host) or numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+class Handle:
+    """One problem on the current CUDA device (sbec_create / sbec_destroy)."""
+
+    def __init__(self, F, n, lo, hi, beta, M, p=0.0, q=0.0, V=None, precision="fp64",
+                 stream=None):
+        n = tuple(int(v) for v in n)
+        dim = len(n)
+        pr = Problem()
+        pr.F, pr.dim = int(F), dim
+        for i in range(3):
+            pr.n[i] = n[i] if i < dim else 1
+            pr.lo[i] = float(lo[i]) if i < dim else 0.0
+            pr.hi[i] = float(hi[i]) if i < dim else 1.0
+        b = tuple(beta) + (0.0,) * (4 - len(beta))
+        for i in range(4):
+            pr.beta[i] = float(b[i])
+        pr.p, pr.q, pr.M = float(p), float(q), float(M)
+        pr.precision = FP64 if precision == "fp64" else MIXED
+        self.problem = pr
+        self.F, self.C, self.n, self.dim = int(F), 2 * int(F) + 1, n, dim
+        self.precision = precision
+        self.shape = (self.C,) + tuple(reversed(n))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        if V is not None:
+            if isinstance(V, np.ndarray):
+                V = np.ascontiguousarray(V, dtype=np.float64)
+            self._V_keep = V
+        out = _vp()
+        _check(_lib.sbec_create(ctypes.byref(pr), _ptr(V) if V is not None else None, stream,
+                                ctypes.byref(out)), "sbec_create")
+        self._h = out
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", V="auto", stream=None):
+        from . import workloads as W
+        if isinstance(V, str) and V == "auto":
+            V = W.potential(w)
+        return cls(w.F, w.n, w.lo, w.hi, w.beta, w.M, p=w.p, q=w.q, V=V,
+                   precision=precision, stream=stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sbec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -------------------------------------------------------------
+    def energy(self, X, sync=True):
+        E = ctypes.c_double()
+        _check(_lib.sbec_energy(self._h, _ptr(X), ctypes.byref(E) if sync else None), "sbec_energy")
+        return E.value if sync else None
+
+    def grad(self, X, G_euc=None, G_riem=None, sync=True):
+        """Returns (E, ||grad E||_2) when sync, else None (values stay on the device)."""
+        E, rn = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.sbec_grad(self._h, _ptr(X), _ptr(G_euc), _ptr(G_riem),
+                              ctypes.byref(E) if sync else None,
+                              ctypes.byref(rn) if sync else None), "sbec_grad")
+        return (E.value, rn.value) if sync else None
+
+    def hessvec(self, X, Z, HZ, sigma=0.0, riemannian=False):
+        _check(_lib.sbec_hessvec(self._h, _ptr(X), _ptr(Z), float(sigma), int(bool(riemannian)),
+                                 _ptr(HZ)), "sbec_hessvec")
+
+    def retract(self, U, Xi, t, kind, out):
+        _check(_lib.sbec_retract(self._h, _ptr(U), _ptr(Xi), float(t), int(kind), _ptr(out)),
+               "sbec_retract")
+
+    def sync(self):
+        _check(_lib.sbec_sync(self._h), "sbec_sync")
+
+    def sync_status(self):
+        return _lib.sbec_sync(self._h)
+
+    def scalars_ptr(self):
+        return _lib.sbec_scalars(self._h)
+
+    def launch_count(self):
+        return int(_lib.sbec_launch_count(self._h))
+
+    def profile(self, enable=True):
+        _check(_lib.sbec_profile(self._h, int(bool(enable))), "sbec_profile")
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} of the launches recorded since profile(True)."""
+        mx = 64
+        names = ctypes.create_string_buffer(32 * mx)
+        ms = (ctypes.c_double * mx)()
+        cnt = (ctypes.c_longlong * mx)()
+        rows = _int()
+        _check(_lib.sbec_profile_read(self._h, mx, names, ms, cnt, ctypes.byref(rows)),
+               "sbec_profile_read")
+        out = {}
+        for r in range(rows.value):
+            nm = names.raw[32 * r: 32 * r + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (ms[r], int(cnt[r]))
+        return out
+
+
+def library_symbols():
+    """Names of the exported entry points that resolve in the loaded library."""
+    return [name for name in EXPORTED if hasattr(_lib, name)]

@@ -1,0 +1,176 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs: energy (Eq. 3.7), Euclidean gradient
+(Eq. 3.12), Riemannian gradient (Lemma 4.1), Hessian-vector products
+(Eq. 3.13, Lemma 4.2) and the three retractions (Lemmas 5.1, 5.3, 5.4).
+
+Bars: FP64 form 1e-12 relative (normwise for fields); mixed form (FP32 FFT and
+pointwise arithmetic, FP64 reductions) 2e-6 relative for energies and 2e-5
+normwise for fields (derived from the float unit roundoff 6e-8 times the
+log2(G) FFT depth and the conditioning of the nonlinear terms)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sbec_oracle as O  # noqa: E402
+from paper_1907_01194_gb300 import workloads as W  # noqa: E402
+from tests.gpu_helpers import case_inputs, rel  # noqa: E402
+
+
+def _sbec():
+    from paper_1907_01194_gb300 import sbec
+    return sbec
+
+
+def _wl(F, n, L, M, beta, lattice=0.0, p=0.0, q=0.0):
+    d = len(n)
+    return W.Workload(f"par_F{F}_{'x'.join(map(str, n))}", F=F, n=tuple(n), lo=(-L,) * d, hi=(L,) * d,
+                      beta=beta, M=M, p=p, q=q, lattice_amp=lattice, lattice_k=math.pi / 2)
+
+
+CASES = [
+    _wl(1, (256,), 16.0, 0.5, (100.0, -0.5, 0, 0)),                      # 1D, spin-1
+    _wl(3, (8,), 4.0, 0.7, (30.0, 1.0, 2.0, -1.0), p=0.2, q=0.1),       # tiny 1D
+    _wl(2, (64, 32), 8.0, 0.3, (200.0, 10.0, -5.0, 0), lattice=20.0),     # 2D non-square
+    _wl(3, (16, 64), 6.0, 1.1, (60.0, -2.0, 5.0, -1.0), lattice=3.0),     # 2D spin-3
+    _wl(1, (2, 256), 5.0, 0.2, (50.0, 1.0, 0, 0)),                        # degenerate x axis
+    _wl(3, (16, 8, 32), 6.0, 0.2, (500.0, -2.0, 5.0, -1.0)),              # 3D non-cubic
+    _wl(2, (32, 32, 32), 8.0, 0.0, (100.0, 3.0, 4.0, 0), lattice=10.0),   # 3D, M = 0
+    _wl(1, (1024,), 20.0, 0.4, (300.0, 2.0, 0, 0)),                       # longest axis
+]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("w", CASES, ids=lambda w: w.name)
+def test_fp64_energy_grad_hess_parity(w, dev):
+    sbec = _sbec()
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    Z = torch.from_numpy(Zf).to(dev)
+    Ge, Gr, H1, H2 = (torch.empty_like(X) for _ in range(4))
+    with sbec.Handle.from_workload(w) as h:
+        E1 = h.energy(X)
+        E2, rn = h.grad(X, G_euc=Ge, G_riem=Gr)
+        h.hessvec(X, Z, H1, sigma=0.3, riemannian=False)
+        h.hessvec(X, Z, H2, sigma=0.3, riemannian=True)
+        h.sync()
+    Xm = O.from_u(P, u)
+    E_ref = O.energy(P, Xm)
+    assert abs(E1 - E_ref) <= 1e-12 * abs(E_ref)
+    assert abs(E2 - E_ref) <= 1e-12 * abs(E_ref)
+    g = O.gradient(P, Xm)
+    assert rel(Ge.cpu().numpy(), O.to_fields(P, g)) <= 1e-12
+    rg = O.rgrad(P, u, O.to_u(P, g))
+    assert rel(Gr.cpu().numpy(), O.to_fields(P, O.from_u(P, rg))) <= 1e-11 * max(1.0, np.linalg.norm(O.to_u(P, g)) / np.linalg.norm(rg))
+    assert abs(rn - np.linalg.norm(rg)) <= 1e-11 * np.linalg.norm(O.to_u(P, g))
+    Zm = O.to_matrix(P, Zf)
+    H_ref = O.hessvec(P, Xm, Zm) + 0.3 * Zm
+    assert rel(H1.cpu().numpy(), O.to_fields(P, H_ref)) <= 1e-12
+    Hr_ref = O.rhess(P, u, O.to_u(P, Zm), g=O.to_u(P, g), sigma=0.3)
+    assert rel(H2.cpu().numpy(), O.to_fields(P, O.from_u(P, Hr_ref))) <= 1e-11
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[6]], ids=lambda w: w.name)
+def test_fp64_retraction_parity(w, kind, dev):
+    sbec = _sbec()
+    P, u, Xf, Zf = case_inputs(w)
+    xi = O.project(P, u, O.to_u(P, O.to_matrix(P, Zf)))
+    xi /= np.linalg.norm(xi)
+    Xi = O.to_fields(P, O.from_u(P, xi))
+    U = torch.from_numpy(Xf).to(dev)
+    XiD = torch.from_numpy(Xi).to(dev)
+    out = torch.empty_like(U)
+    with sbec.Handle.from_workload(w) as h:
+        for t in (0.3, 1e-3):
+            h.retract(U, XiD, t, kind, out)
+            h.sync()
+            ref = O.retract(P, u, t * xi, kind)
+            assert rel(out.cpu().numpy(), O.to_fields(P, O.from_u(P, ref))) <= 1e-12
+            got = O.to_u(P, O.to_matrix(P, out.cpu().numpy()))
+            Gm = O.gamma_weights(P)
+            assert abs(got @ got - 1) < 1e-12 and abs(got @ (Gm * got) - w.M) < 1e-12
+
+
+@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5]], ids=lambda w: w.name)
+def test_mixed_precision_bound(w, dev):
+    sbec = _sbec()
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf.astype(np.complex64)).to(dev)
+    Z = torch.from_numpy(Zf.astype(np.complex64)).to(dev)
+    Ge, H1 = torch.empty_like(X), torch.empty_like(X)
+    with sbec.Handle.from_workload(w, precision="mixed") as h:
+        E = h.energy(X)
+        E2, rn = h.grad(X, G_euc=Ge)
+        h.hessvec(X, Z, H1, sigma=0.0, riemannian=False)
+        h.sync()
+    # the oracle sees the same float-rounded inputs
+    Xm = O.to_matrix(P, Xf.astype(np.complex64).astype(np.complex128))
+    Zm = O.to_matrix(P, Zf.astype(np.complex64).astype(np.complex128))
+    E_ref = O.energy(P, Xm)
+    assert abs(E - E_ref) <= 2e-6 * abs(E_ref)
+    assert abs(E2 - E_ref) <= 2e-6 * abs(E_ref)
+    assert rel(Ge.cpu().numpy(), O.to_fields(P, O.gradient(P, Xm))) <= 2e-5
+    assert rel(H1.cpu().numpy(), O.to_fields(P, O.hessvec(P, Xm, Zm))) <= 2e-5
+
+
+def test_host_pointers_match_device(dev):
+    sbec = _sbec()
+    w = CASES[2]
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    Gd = torch.empty_like(X)
+    Gh = np.empty_like(Xf)
+    with sbec.Handle.from_workload(w) as h:
+        Ed, rd = h.grad(X, G_riem=Gd)
+        Eh, rh = h.grad(np.ascontiguousarray(Xf), G_riem=Gh)
+    assert Ed == Eh and rd == rh
+    assert np.array_equal(Gd.cpu().numpy(), Gh)
+
+
+def test_deterministic_repeat(dev):
+    sbec = _sbec()
+    w = CASES[5]
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    with sbec.Handle.from_workload(w) as h:
+        a = h.grad(X)
+        b = h.grad(X)
+    assert a == b
+
+
+def test_error_codes(dev):
+    sbec = _sbec()
+    with pytest.raises(sbec.SbecError) as e:
+        sbec.Handle(1, (64,), (-8,), (8,), (10.0, 1.0), M=1.0)        # |M| >= F
+    assert e.value.status == sbec.ERR_ARG
+    with pytest.raises(sbec.SbecError):
+        sbec.Handle(1, (48,), (-8,), (8,), (10.0, 1.0), M=0.2)        # n not a power of two
+    w = CASES[0]
+    P, u, Xf, Zf = case_inputs(w)
+    U = np.array(Xf, copy=True)
+    U[1:] = 0                                                         # only l = 1 left: outside Omega
+    Xi = np.zeros_like(U)
+    out = np.empty_like(U)
+    with sbec.Handle.from_workload(w) as h:
+        for kind in (1, 2, 3):
+            with pytest.raises(sbec.SbecError) as e:
+                h.retract(U, Xi, 0.0, kind, out)
+            assert e.value.status == sbec.ERR_DOMAIN
+        bad = np.array(Xf, copy=True)
+        bad[0, 3] = np.nan
+        with pytest.raises(sbec.SbecError) as e:
+            h.grad(bad)
+        assert e.value.status == sbec.ERR_NONFINITE
+        # the handle stays usable after an error
+        E, rn = h.grad(np.array(Xf, copy=True))
+        assert math.isfinite(E)
