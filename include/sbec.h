@@ -125,6 +125,28 @@ long long sbec_launch_count(const sbec_handle* h);
 int sbec_profile(sbec_handle* h, int enable);
 int sbec_profile_read(sbec_handle* h, int max, char* names, double* ms, long long* counts, int* rows);
 
+/* Allocation-free energy (the paper has no counterpart: this is a service of
+ * the library).  For callers that must not allocate device memory when they
+ * need the energy, for example a host framework that owns all device memory
+ * through its own pool, or a latency-critical loop that cannot afford
+ * cudaMalloc/cudaFree (which can wait for the whole device to go idle).
+ * Computes E_h(X) (Eq. 3.7) like sbec_energy but without a handle: every
+ * intermediate lives in one fixed 8 MiB array of device memory inside the
+ * library image, which each GPU that loads the library holds until the process
+ * exits.  prob must have precision SBEC_FP64; V is a device array of G doubles
+ * or NULL for the harmonic trap; X is a device array in the state layout; E is
+ * a host pointer; the call runs on cuda_stream and synchronises it.  The array
+ * holds 2^20 doubles: the transformed field (2 C G doubles), the harmonic
+ * potential when V is NULL (G), and about 40,000 doubles of tables and partial
+ * sums; a problem that needs more is rejected with SBEC_ERR_ARG (spin-3 on
+ * 256 x 256 fits, spin-3 on 512 x 256 does not).  The first call on a device looks up the
+ * array's device address, so make it before any stream capture.  All calls
+ * share the one array and leave their intermediates in it: calls that overlap
+ * on the GPU (other streams or host threads) race and must be serialised by
+ * the caller. */
+int sbec_energy_noalloc(const sbec_problem* prob, const double* V, const void* X, double* E,
+                        void* cuda_stream);
+
 #define SBEC_S_ENERGY      0   /* E_h of the latest energy / grad call */
 #define SBEC_S_RGRAD_NORM2 1   /* ||grad E||^2 of the latest grad call */
 #define SBEC_S_ALPHA_G     2   /* Lemma 4.2 alpha_g of the latest grad call */

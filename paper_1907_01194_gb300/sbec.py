@@ -204,3 +204,32 @@ class Handle:
 def library_symbols():
     """Names of the exported entry points that resolve in the loaded library."""
     return [name for name in EXPORTED if hasattr(_lib, name)]
+
+
+_lib.sbec_energy_noalloc.argtypes = [ctypes.POINTER(Problem), _vp, _vp, _dp, _vp]
+_lib.sbec_energy_noalloc.restype = _int
+
+
+def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
+    """E_h(X) through sbec_energy_noalloc: no handle and no device allocation, for
+    callers that cannot allocate device memory where they need the energy.  X and
+    V (None: harmonic trap) must be device tensors; FP64 only."""
+    n = tuple(int(v) for v in n)
+    dim = len(n)
+    pr = Problem()
+    pr.F, pr.dim = int(F), dim
+    for i in range(3):
+        pr.n[i] = n[i] if i < dim else 1
+        pr.lo[i] = float(lo[i]) if i < dim else 0.0
+        pr.hi[i] = float(hi[i]) if i < dim else 1.0
+    b = tuple(beta) + (0.0,) * (4 - len(beta))
+    for i in range(4):
+        pr.beta[i] = float(b[i])
+    pr.p, pr.q, pr.M, pr.precision = float(p), float(q), float(M), FP64
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    E = ctypes.c_double()
+    _check(_lib.sbec_energy_noalloc(ctypes.byref(pr), _ptr(V), _ptr(X), ctypes.byref(E), stream),
+           "sbec_energy_noalloc")
+    return E.value
