@@ -105,6 +105,49 @@ int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int
  * is outside Omega (kinds 1, 2) or S (kind 3). */
 int sbec_retract(sbec_handle* h, const void* U, const void* Xi, double t, int kind, void* out);
 
+/* Ground-state solve (Sec. 5, Algorithm 1 on one mesh): the Riemannian
+ * gradient method with BB step and nonmonotone search (RGBB) as a warm start,
+ * then the adaptive regularised Newton method (ARNT) with the modified CG,
+ * the curvilinear search and the sigma update of Sec. 7.1; or RGBB alone.
+ * Readings where the paper is silent (constants of the modified CG and of the
+ * searches) follow the library's design notes and match its CPU oracle. */
+#define SBEC_ARNT 0
+#define SBEC_RGBB 1
+
+typedef struct sbec_solve_opts {
+    int    method;           /* SBEC_ARNT (RGBB warm start, then ARNT) or SBEC_RGBB */
+    int    retraction;       /* 1 (projective, the paper's choice), 2 or 3 */
+    double tol;              /* stop when ||grad E||_2 <= tol (Sec. 7.1 uses 1e-6) */
+    int    maxit;            /* iteration cap of the final method (Sec. 7.1: 10000) */
+    double rgbb_tol;         /* warm-start tolerance inside ARNT (Sec. 7.1: 1e-2) */
+    int    rgbb_maxit;       /* warm-start cap inside ARNT (Sec. 7.1: 2000) */
+    int    project_initial;  /* 1: replace X by P_M(X) (Lemma 5.1) before iterating */
+} sbec_solve_opts;
+
+typedef struct sbec_stats {
+    double    energy;        /* E_h at the returned state */
+    double    grad_norm;     /* ||grad E||_2 at the returned state */
+    long long outer_iters;   /* ARNT (or RGBB-only) iterations */
+    long long inner_iters;   /* modified-CG iterations in total */
+    long long rgbb_iters;    /* RGBB iterations (warm start included) */
+    long long n_grad, n_energy, n_hvp;
+    int       converged;     /* grad_norm <= tol */
+} sbec_stats;
+
+/* Paper defaults: ARNT with R1, tol 1e-6, maxit 10000, RGBB warm start to 1e-2
+ * or 2000 iterations, project_initial 1. */
+void sbec_solve_defaults(sbec_solve_opts* opts);
+
+/* Bytes of device workspace sbec_solve needs for the handle's problem (ten fields). */
+int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes);
+
+/* Minimise E_h over M from X (host or device array, overwritten with the
+ * solution).  workspace: caller-owned device memory of at least
+ * sbec_solve_workspace_bytes.  Returns SBEC_OK, SBEC_ERR_NOCONV (cap reached,
+ * X holds the last iterate) or an error.  Synchronises the stream. */
+int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+               sbec_stats* stats);
+
 /* Stream synchronisation; returns the first device-side error recorded since
  * the previous sbec_sync (and clears it), or SBEC_ERR_CUDA. */
 int sbec_sync(sbec_handle* h);

@@ -9,22 +9,7 @@
 #include "sbec.h"
 #include "sbec_internal.h"
 
-struct sbec_handle {
-    sbec_problem prob;
-    sbec::Geom geom;
-    sbec::Work work;
-    cudaStream_t stream;
-    int device;
-    size_t elem;          // bytes of one complex value
-    size_t field_bytes;   // C * G * elem
-    void* d_tw;
-    double* d_lam2;
-    void* d_V;
-    void* stage[3];
-    double* h_scal;       // pinned mirror of the scalar block
-    const void* last_grad_X;
-    sbec::Prof prof;
-};
+#include "sbec_handle.h"
 
 namespace sbec {
 
@@ -98,6 +83,13 @@ void* stage_out_ptr(sbec_handle* h, void* p, int slot, bool* host) {
     *host = true;
     return h->stage[slot];
 }
+
+}  // namespace
+
+int sbec_read_scalars(sbec_handle* h) { return read_scalars(h); }
+bool sbec_is_device_ptr(const void* p) { return is_device_ptr(p); }
+
+namespace {
 
 int copy_back(sbec_handle* h, void* user, void* dev) {
     if (user && user != dev) TRY_CUDA(cudaMemcpyAsync(user, dev, h->field_bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -278,7 +270,7 @@ long long sbec_launch_count(const sbec_handle* h) { return h ? h->prof.launches 
 static const char* kKernelNames[sbec::K_COUNT] = {
     "x_fwd", "x_fwd_energy", "x_inv_grad", "x_inv_hess", "x_full_grad", "x_full_energy", "x_full_hess",
     "s_fwd", "s_inv", "s_k2", "s_parseval", "dot_reduce", "proj_apply", "retract_w", "scale", "finalize",
-    "retract_solve", "tables"};
+    "retract_solve", "tables", "lincomb", "prolong"};
 
 int sbec_profile(sbec_handle* h, int enable) {
     if (!h) return SBEC_ERR_ARG;

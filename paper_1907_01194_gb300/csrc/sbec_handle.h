@@ -1,0 +1,29 @@
+// The handle behind the opaque sbec_handle of the C ABI (shared by the C-ABI
+// and solver translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sbec.h"
+#include "sbec_internal.h"
+
+struct sbec_handle {
+    sbec_problem prob;
+    sbec::Geom geom;
+    sbec::Work work;
+    cudaStream_t stream;
+    int device;
+    size_t elem;          // bytes of one complex value
+    size_t field_bytes;   // C * G * elem
+    void* d_tw;
+    double* d_lam2;
+    void* d_V;
+    void* stage[3];
+    double* h_scal;       // pinned mirror of the scalar block
+    const void* last_grad_X;
+    sbec::Prof prof;
+};
+
+// helpers of the C-ABI translation unit used by the solver
+int sbec_read_scalars(sbec_handle* h);
+bool sbec_is_device_ptr(const void* p);

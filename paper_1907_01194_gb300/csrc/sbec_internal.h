@@ -40,7 +40,7 @@ struct Geom {
 enum KernelId {
     K_X_FWD, K_X_FWD_EPW, K_X_INV_GRAD, K_X_INV_HESS, K_X_FULL_GRAD, K_X_FULL_ENERGY, K_X_FULL_HESS,
     K_S_FWD, K_S_INV, K_S_K2, K_S_PARSEVAL, K_DOT, K_PROJ, K_RETW, K_SCALE, K_FIN, K_RSOLVE, K_TABLES,
-    K_COUNT
+    K_LIN, K_PROLONG, K_COUNT
 };
 
 // Launch bookkeeping of one handle: every library kernel launch is counted;
@@ -77,8 +77,30 @@ struct Work {
     Prof* prof;
 };
 
+// out = (ca * scal[ia]) A + (cb * scal[ib]) B over the 2 C G reals of a field, with
+// optional fused dots <out, D1>, <out, D2>; skipped (out left as is, dots of the
+// old out) when scal[guard] == 0.
+struct Lin {
+    void* out;
+    const void* A;
+    const void* B;
+    double ca, cb;
+    int ia, ib;
+    int ineg;
+    const void* D1;
+    const void* D2;
+    int guard;
+};
+
 // per-precision entry points (implemented in sbec_kernels_f64.cu / _f32.cu)
 template <typename T> struct Ops {
+    static int lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s);
+    static int dot2(const Geom& g, const Work& w, const void* A, const void* B, const void* C, const void* D,
+                    int slot, cudaStream_t s);
+    static int bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
+                      int slot, cudaStream_t s);
+    static int ratio(const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
+                     cudaStream_t s);
     static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
     static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
                     cudaStream_t s);

@@ -367,12 +367,33 @@ static __device__ __forceinline__ void set_status(double* scal, int code) {
     if (scal[SBEC_S_STATUS] == 0.0) scal[SBEC_S_STATUS] = double(code);
 }
 
-// energy: scal[E] = sum(partA q0) + sum(partB q0)   (1D: partA q0 + partA q1)
+// Warp-parallel fixed-order sums: warp w of the block reduces quantities
+// q = w, w + nwarps, ...; lane-strided loads then a shuffle tree, so each sum
+// has a fixed order for a given nblk.  vals[q] is valid after the barrier.
+__device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int na, const int* qs, int nq,
+                                          double* vals) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nq; k += nw) {
+        const double* src = pa + (size_t)qs[k] * na;
+        double s = 0.0;
+        for (int i = lane; i < na; i += 32) s += src[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) vals[k] = s;
+    }
+    __syncthreads();
+}
+
+// energy: scal[E] = sum of partA quantities 0..nqa-1 (+ partB quantity 0)
 static __global__ void k_fin_energy(const double* pa, int na, int nqa, const double* pb, int nb, double* scal) {
-    double e = 0.0;
-    for (int q = 0; q < nqa; ++q) e += block_sum_partials(pa, q, na);
-    if (pb) e += block_sum_partials(pb, 0, nb);
+    __shared__ double va[4], vb[1];
+    const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
+    warp_sums(pa, na, qa, nqa, va);
+    if (pb) warp_sums(pb, nb, qb, 1, vb);
     if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int q = 0; q < nqa; ++q) e += va[q];
+        if (pb) e += vb[0];
         scal[SBEC_S_ENERGY] = e;
         if (!isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
     }
@@ -382,18 +403,22 @@ static __global__ void k_fin_energy(const double* pa, int na, int nqa, const dou
 // t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
 // beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
 static __global__ void k_fin_proj(const double* pa, int na, int F, int qe, int qn, int qt, double M, double* scal,
-                           int slot_a, int slot_b, int write_grad_info) {
+                                  int slot_a, int slot_b, int write_grad_info) {
     const int C = 2 * F + 1;
-    double e = 0.0, a = 0.0, b = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
-    if (qe >= 0) e = block_sum_partials(pa, qe, na);
-    for (int i = 0; i < C; ++i) {
-        const double l = double(F - i);
-        const double nl = block_sum_partials(pa, qn + i, na);
-        const double tl = block_sum_partials(pa, qt + i, na);
-        a += nl; b += l * nl; c += l * l * nl;
-        ug += tl; uGg += l * tl;
-    }
+    __shared__ double v[15];
+    int qs[15];
+    int nq = 0;
+    for (int i = 0; i < C; ++i) qs[nq++] = qn + i;
+    for (int i = 0; i < C; ++i) qs[nq++] = qt + i;
+    if (qe >= 0) qs[nq++] = qe;
+    warp_sums(pa, na, qs, nq, v);
     if (threadIdx.x == 0) {
+        double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, b = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
+        for (int i = 0; i < C; ++i) {
+            const double l = double(F - i), nl = v[i], tl = v[C + i];
+            a += nl; b += l * nl; c += l * l * nl;
+            ug += tl; uGg += l * tl;
+        }
         const double au = c - M * M;
         const double al = (c * ug - M * uGg) / au;
         const double be = (uGg - M * ug) / au;
@@ -412,30 +437,34 @@ static __global__ void k_fin_proj(const double* pa, int na, int F, int qe, int q
 }
 
 static __global__ void k_fin_norm(const double* pa, int na, double* scal, int slot) {
-    const double s = block_sum_partials(pa, 0, na);
+    __shared__ double v[1];
+    const int q[1] = {0};
+    warp_sums(pa, na, q, 1, v);
     if (threadIdx.x == 0) {
-        scal[slot] = s;
-        if (!isfinite(s)) set_status(scal, SBEC_ERR_NONFINITE);
+        scal[slot] = v[0];
+        if (!isfinite(v[0])) set_status(scal, SBEC_ERR_NONFINITE);
     }
 }
 
-// Retraction scales sigma_l from m_l = |w_l|^2 (Sec. 6).  kind 1: Lemma 5.1 (r is
-// the zero of the increasing h1 on (1/(f1-M), 1/(f2-M)): bisection, then Newton);
-// kind 2: Lemma 5.3 (r the positive zero of h3 = h2 t^{-f1-F}: doubling bracket,
-// bisection, Newton); kind 3: Lemma 5.4 closed form.
+// Retraction scales sigma_l from m_l = |w_l|^2 (Sec. 6).
+//  kind 1, Lemma 5.1: r is the zero of h1, increasing on (1/(f1-M), 1/(f2-M))
+//    (Eq. hderi); safeguarded Newton from r = 0 (the zero for w on M), bisecting
+//    whenever a Newton step leaves the current sign bracket.
+//  kind 2, Lemma 5.3: r is the positive zero of h3 = h2 t^{-f1-F}, h3(0) < 0 and
+//    h3' > 0 at the zero; bracket from t = 1 by doubling / halving, then the same
+//    safeguarded Newton.
+//  kind 3, Lemma 5.4: closed form.
+// Both iterations stop when the step is below 4 ulps of r or after 200 steps.
 static __global__ void k_retract_solve(const double* pa, int na, int F, double M, int kind, double* scal) {
     __shared__ double m[7];
     const int C = 2 * F + 1;
-    for (int i = 0; i < C; ++i) {
-        const double v = block_sum_partials(pa, i, na);
-        if (threadIdx.x == 0) m[i] = v;
-    }
-    __syncthreads();
+    const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
+    warp_sums(pa, na, qs, C, m);
     if (threadIdx.x != 0) return;
     double sig[7];
     for (int i = 0; i < 7; ++i) sig[i] = 0.0;
-    // f1 = min l with w_l != 0, f2 = max
-    int i1 = -1, i2 = -1;  // component indices of f2 (smallest index) and f1 (largest index)
+    // f2 = largest l with w_l != 0 (component index i1), f1 = smallest (index i2)
+    int i1 = -1, i2 = -1;
     for (int i = 0; i < C; ++i)
         if (m[i] > 0.0) { if (i1 < 0) i1 = i; i2 = i; }
     bool ok = (i1 >= 0);
@@ -451,72 +480,77 @@ static __global__ void k_retract_solve(const double* pa, int na, int F, double M
         }
     } else if (ok && f1 < M && M < f2) {
         if (kind == 1) {
-            double lo = 1.0 / (f1 - M), hi = 1.0 / (f2 - M);
-            const double lo0 = lo, hi0 = hi;
-            for (int it = 0; it < 400; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (!(mid > lo && mid < hi)) break;
-                double h1 = 0.0;
+            double lo = 1.0 / (f1 - M), hi = 1.0 / (f2 - M);   // h1(lo+) = -inf, h1(hi-) = +inf
+            double r = 0.0;
+            for (int it = 0; it < 200; ++it) {
+                double h = 0.0, dh = 0.0;
                 for (int i = i1; i <= i2; ++i) {
-                    const double d = double(F - i) - M, q = 1.0 - d * mid;
-                    h1 += d * m[i] / (q * q);
+                    const double d = double(F - i) - M, q = 1.0 - d * r, iq = 1.0 / q;
+                    const double t = d * m[i] * iq * iq;
+                    h += t;
+                    dh += 2.0 * d * t * iq;
                 }
-                if (h1 < 0.0) lo = mid; else hi = mid;
-            }
-            double r = 0.5 * (lo + hi);
-            for (int it = 0; it < 3; ++it) {
-                double h1 = 0.0, dh = 0.0;
-                for (int i = i1; i <= i2; ++i) {
-                    const double d = double(F - i) - M, q = 1.0 - d * r;
-                    h1 += d * m[i] / (q * q);
-                    dh += 2.0 * d * d * m[i] / (q * q * q);
-                }
-                if (dh > 0.0) {
-                    const double rn = r - h1 / dh;
-                    if (rn > lo0 && rn < hi0) r = rn;
-                }
+                if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
+                double rn = (dh > 0.0) ? r - h / dh : 0.5 * (lo + hi);
+                if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
+                const double step = fabs(rn - r);
+                r = rn;
+                if (step <= 4.0 * 2.220446049250313e-16 * fmax(fabs(r), 1e-300)) break;
             }
             double s = 0.0;
             for (int i = i1; i <= i2; ++i) {
                 const double q = 1.0 - (double(F - i) - M) * r;
                 s += m[i] / (q * q);
             }
-            for (int i = i1; i <= i2; ++i) sig[i] = 1.0 / (sqrt(s) * (1.0 - (double(F - i) - M) * r));
+            const double rs = 1.0 / sqrt(s);
+            for (int i = i1; i <= i2; ++i) sig[i] = rs / (1.0 - (double(F - i) - M) * r);
         } else {
-            // h3(t) = sum_{j} (j + f1 - M) m_{f1 + j} t^j, component of l = f1 + j is F - f1 - j
+            // h3(t) = sum_j (j + f1 - M) m_{f1+j} t^j over j = 0..f2-f1 (component index F - f1 - j)
+            const int jmax = int(f2 - f1), i0 = F - int(f1);
             auto h3 = [&](double t, double* dh) {
-                double v = 0.0, dv = 0.0, tp = 1.0, tpm = 0.0;
-                const int jmax = int(f2 - f1);
-                for (int j = 0; j <= jmax; ++j) {
-                    const int i = F - int(f1) - j;
-                    const double cf = (double(j) + f1 - M) * m[i];
-                    v += cf * tp;
-                    dv += double(j) * cf * tpm;
-                    tpm = tp;
-                    tp *= t;
+                double v = 0.0, dv = 0.0;
+                for (int j = jmax; j >= 0; --j) {          // Horner for h3 and h3'
+                    const double cf = (double(j) + f1 - M) * m[i0 - j];
+                    dv = dv * t + v;
+                    v = v * t + cf;
                 }
-                if (dh) *dh = dv;
+                *dh = dv;
                 return v;
             };
+            double dh;
             double lo = 0.0, hi = 1.0;
             int guard = 0;
-            while (h3(hi, nullptr) <= 0.0 && guard < 2000) { lo = hi; hi *= 2.0; ++guard; }
+            if (h3(1.0, &dh) < 0.0) {
+                lo = 1.0; hi = 2.0;
+                while (h3(hi, &dh) < 0.0 && guard++ < 2000) { lo = hi; hi *= 2.0; }
+            }
             if (guard >= 2000) ok = false;
-            for (int it = 0; it < 2000 && ok; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (!(mid > lo && mid < hi)) break;
-                if (h3(mid, nullptr) < 0.0) lo = mid; else hi = mid;
+            double r = (lo > 0.0) ? lo : 1.0;
+            for (int it = 0; it < 200 && ok; ++it) {
+                const double h = h3(r, &dh);
+                if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
+                double rn = (dh > 0.0) ? r - h / dh : 0.5 * (lo + hi);
+                if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
+                const double step = fabs(rn - r);
+                r = rn;
+                if (step <= 4.0 * 2.220446049250313e-16 * r) break;
             }
-            double r = 0.5 * (lo + hi);
-            for (int it = 0; it < 3 && ok; ++it) {
-                double dh;
-                const double v = h3(r, &dh);
-                if (dh > 0.0) { const double rn = r - v / dh; if (rn > 0.0) r = rn; }
-            }
+            // sigma_0^2 = 1 / sum_l m_l r^l, sigma_l = sigma_0 r^{l/2}
+            const double sr = sqrt(r), isr = 1.0 / sr;
             double ssum = 0.0;
-            for (int i = 0; i < C; ++i) ssum += m[i] * pow(r, double(F - i));
+            for (int i = 0; i < C; ++i) {
+                const int l = F - i;
+                double p = 1.0;
+                for (int k = 0; k < (l > 0 ? l : -l); ++k) p *= (l > 0 ? r : 1.0 / r);
+                ssum += m[i] * p;
+            }
             const double s0 = sqrt(1.0 / ssum);
-            for (int i = 0; i < C; ++i) sig[i] = s0 * pow(r, 0.5 * double(F - i));
+            for (int i = 0; i < C; ++i) {
+                const int l = F - i;
+                double p = 1.0;
+                for (int k = 0; k < (l > 0 ? l : -l); ++k) p *= (l > 0 ? sr : isr);
+                sig[i] = s0 * p;
+            }
         }
     } else {
         ok = false;
@@ -526,6 +560,100 @@ static __global__ void k_retract_solve(const double* pa, int na, int F, double M
         scal[S_SIG + i] = sig[i];
     }
     if (!ok) set_status(scal, SBEC_ERR_DOMAIN);
+}
+
+// ---------------------------------------------------------------------------
+// Tangent-vector BLAS-1 (Sec. 4 inner product <xi, zeta>_u = xi^T zeta on the real
+// stacking, Eq. prod): fields are treated as 2 C G reals.  Dots go to per-block
+// partials (fixed order); coefficients are read from the scalar block so that a
+// sequence of updates needs no host round trip.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const double* __restrict__ scal,
+                                                 double* partials, int nblk) {
+    // out may alias A, B, D1 or D2 (same index only), so no __restrict__ here
+    const T* A = reinterpret_cast<const T*>(L.A);
+    const T* B = reinterpret_cast<const T*>(L.B);
+    const T* D1 = reinterpret_cast<const T*>(L.D1);
+    const T* D2 = reinterpret_cast<const T*>(L.D2);
+    T* O = reinterpret_cast<T*>(L.out);
+    const bool self1 = (L.D1 == L.out), self2 = (L.D2 == L.out);
+    double ca = L.ca, cb = L.cb;
+    if (L.ia >= 0) ca *= scal[L.ia];
+    if (L.ib >= 0) cb *= scal[L.ib];
+    const bool upd = (L.guard < 0) || (scal[L.guard] != 0.0);
+    const T a = T(ca), b = T(cb);
+    double acc[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        T v;
+        if (upd) {
+            v = a * A[i];
+            if (B) v += b * B[i];
+            O[i] = v;
+        } else {
+            v = O[i];
+        }
+        if (D1) acc[0] += double(v) * (self1 ? double(v) : double(D1[i]));
+        if (D2) acc[1] += double(v) * (self2 ? double(v) : double(D2[i]));
+    }
+    if (partials) block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+}
+
+// partials q0 = <A, B>, q1 = <C, D> (C null: skip)
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, const void* Cp, const void* Dp,
+                                              long long N, double* partials, int nblk) {
+    const T* __restrict__ A = reinterpret_cast<const T*>(Ap);
+    const T* __restrict__ B = reinterpret_cast<const T*>(Bp);
+    const T* __restrict__ Cv = reinterpret_cast<const T*>(Cp);
+    const T* __restrict__ D = reinterpret_cast<const T*>(Dp);
+    double acc[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        acc[0] += double(A[i]) * double(B[i]);
+        if (Cv) acc[1] += double(Cv[i]) * double(D[i]);
+    }
+    block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+}
+
+// partials q0 = <u - up, g - gp>, q1 = |g - gp|^2 (the BB quantities s^T v, v^T v)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp, const void* Gp, const void* GPp,
+                                                long long N, double* partials, int nblk) {
+    const T* __restrict__ U = reinterpret_cast<const T*>(Up);
+    const T* __restrict__ UP = reinterpret_cast<const T*>(UPp);
+    const T* __restrict__ G = reinterpret_cast<const T*>(Gp);
+    const T* __restrict__ GP = reinterpret_cast<const T*>(GPp);
+    double acc[2] = {0.0, 0.0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double sv = double(U[i]) - double(UP[i]);
+        const double vv = double(G[i]) - double(GP[i]);
+        acc[0] += sv * vv;
+        acc[1] += vv * vv;
+    }
+    block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+}
+
+// scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2)
+static __global__ void k_fin_sums(const double* pa, int na, int nq, double* scal, int slot) {
+    __shared__ double v[2];
+    const int qs[2] = {0, 1};
+    warp_sums(pa, na, qs, nq, v);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < nq; ++q) {
+            scal[slot + q] = v[q];
+            if (!isfinite(v[q])) set_status(scal, SBEC_ERR_NONFINITE);
+        }
+    }
+}
+
+// scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha, beta)
+static __global__ void k_ratio(double* scal, int dst, int num, int den, int guard_kap, int guard_pp, double eps) {
+    if (threadIdx.x != 0) return;
+    bool ok = true;
+    if (guard_kap >= 0) ok = scal[guard_kap] > eps * scal[guard_pp];
+    scal[dst] = ok ? scal[num] / scal[den] : 0.0;
+    scal[dst + 1] = ok ? 1.0 : 0.0;       // guard flag for the guarded updates
 }
 
 // ---------------------------------------------------------------------------
@@ -895,6 +1023,42 @@ int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi,
 #define R_(F) retract_F<T, F>(g, w, U, Xi, t, kind, out, s)
     SBEC_DISPATCH_F(R_)
 #undef R_
+}
+
+template <typename T>
+int Ops<T>::lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s) {
+    const long long N = 2LL * g.C * g.G;
+    const int nb = elem_blocks(N / 2, w.num_sms);
+    const bool dots = (L.D1 || L.D2);
+    SBEC_LAUNCH(K_LIN, k_lincomb<T>, nb, 256, L, N, w.scal, dots ? w.partB : nullptr, nb);
+    if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, 2, w.scal, dot_slot);
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, const void* C, const void* D, int slot,
+                 cudaStream_t s) {
+    const long long N = 2LL * g.C * g.G;
+    const int nb = elem_blocks(N / 2, w.num_sms);
+    SBEC_LAUNCH(K_DOT, k_dot2<T>, nb, 256, A, B, C, D, N, w.partB, nb);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, C ? 2 : 1, w.scal, slot);
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
+                   int slot, cudaStream_t s) {
+    const long long N = 2LL * g.C * g.G;
+    const int nb = elem_blocks(N / 2, w.num_sms);
+    SBEC_LAUNCH(K_DOT, k_bbdots<T>, nb, 256, U, UP, Gv, GP, N, w.partB, nb);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, 2, w.scal, slot);
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::ratio(const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps, cudaStream_t s) {
+    SBEC_LAUNCH(K_FIN, k_ratio, 1, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps);
+    return SBEC_OK;
 }
 
 template <typename T>

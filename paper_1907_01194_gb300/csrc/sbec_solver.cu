@@ -1,0 +1,332 @@
+// Ground-state solver (Sec. 5, Algorithm 1 on one mesh) driving the device
+// kernels: RGBB (Riemannian gradient, BB step, Zhang-Hager nonmonotone search)
+// and ARNT (regularised Newton model m_k, modified CG, curvilinear Armijo
+// search, ratio test and sigma update).  Every vector operation runs on the
+// device; the host keeps the scalar control flow and reads a small block of
+// scalars once per CG iteration, line-search trial or outer iteration.
+//
+// Readings where the paper defers to the cited ARNT paper or is silent:
+//  * RGBB: first step gamma_0 = 1e-3; BB step |<s,v>|/<v,v> clamped to
+//    [1e-10, 1e10]; rho = 1e-4, varrho = 0.85, delta = 0.2; at most 10
+//    reductions, after which the last trial is taken.
+//  * ARNT: eta1 = 0.01, eta2 = 0.9, gamma0 = 0.2, gamma1 = 1, gamma2 = 10,
+//    sigma_k = sigma_hat_k ||grad||, sigma_hat_0 = 1 (Sec. 7.1); after negative
+//    curvature sigma_{k+1} = max(sigma_{k+1}, sigma_est) (gamma_tilde = 0).
+//  * modified CG: Steihaug-type CG from 0 on Hess m_k[xi] = -grad; stop at
+//    ||r|| <= min(0.1, ||grad||) ||grad||; <p,Hp> <= 1e-12 ||p||^2 ends it: at
+//    the first iteration with s = -grad, later with s = the iterate and d = p
+//    when the curvature is negative; cap 100 inner iterations while
+//    ||grad|| > 1e-3, else 300.
+//  * curvilinear search: alpha0 = 1, delta = 0.2, rho = 1e-4, at most 10
+//    reductions; m_k(z) is evaluated exactly with one Euclidean
+//    Hessian-vector product.  Below the rounding floor 100 eps max(1, |E|)
+//    of E the Armijo test and the ratio are taken as satisfied.
+#include <math.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "sbec_handle.h"
+
+namespace {
+
+using sbec::Lin;
+using sbec::Ops;
+
+// solver slots of the scalar block (pairs: a dot writes slot and slot + 1)
+enum {
+    SL_D0 = sbec::S_SOLVER,       // generic dot pair
+    SL_KAP = SL_D0 + 2,           // <p, Hp>, <p, p>
+    SL_ALPHA = SL_D0 + 4,         // CG alpha and its guard flag
+    SL_RRA = SL_D0 + 6,           // <r, r> of even iterations (pair)
+    SL_RRB = SL_D0 + 8,           // <r, r> of odd iterations (pair)
+    SL_MA = SL_D0 + 10,           // <dz, g>, <dz, dz>
+    SL_MB = SL_D0 + 12,           // <dz, H dz>
+};
+
+constexpr double kEps = 2.220446049250313e-16;
+
+template <typename T>
+struct Solver {
+    sbec_handle* h;
+    const sbec::Geom& g;
+    const sbec::Work& w;
+    cudaStream_t s;
+    sbec_solve_opts o;
+    sbec_stats* st;
+    void* f[10];
+    int status = SBEC_OK;
+
+    Solver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt)
+        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt) {
+        char* b = static_cast<char*>(ws);
+        for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
+    }
+
+    // scalars of the block after the launched work; returns the device status
+    int pull() { return sbec_read_scalars(h); }
+    double sc(int i) const { return h->h_scal[i]; }
+
+    int lin(void* out, double ca, const void* A, double cb, const void* B, int ib = -1, int guard = -1,
+            const void* D1 = nullptr, const void* D2 = nullptr, int slot = SL_D0) {
+        Lin L;
+        L.out = out; L.A = A; L.B = B; L.ca = ca; L.cb = cb; L.ia = -1; L.ib = ib; L.ineg = -1;
+        L.D1 = D1; L.D2 = D2; L.guard = guard;
+        return Ops<T>::lincomb(g, w, L, slot, s);
+    }
+
+    int grad(const void* u, void* gE, void* rg) {
+        ++st->n_grad;
+        return Ops<T>::grad(g, w, u, gE, rg, true, s);
+    }
+    int energy(const void* x) {
+        ++st->n_energy;
+        return Ops<T>::energy(g, w, x, s);
+    }
+    int hess(const void* u, const void* z, double sigma, int riem, void* out) {
+        ++st->n_hvp;
+        return Ops<T>::hessvec(g, w, u, z, sigma, riem, out, s);
+    }
+    int retract(const void* u, const void* xi, double t, void* out) {
+        return Ops<T>::retract(g, w, u, xi, t, o.retraction, out, s);
+    }
+
+#define TRY(x) do { int e_ = (x); if (e_) return e_; } while (0)
+// a device status other than a domain error aborts the solve
+#define PULL(var) do { var = pull(); if (var != SBEC_OK && var != SBEC_ERR_DOMAIN) return var; } while (0)
+
+    // RGBB from u (Sec. 5, Eq. NMN and the C_k, Q_k recursion)
+    int rgbb(void*& u, void*& up, void*& z, void*& rg, void*& rgp, double tol, long long maxit, double& E,
+             double& gn) {
+        int ds;
+        TRY(energy(u));
+        PULL(ds);
+        E = sc(SBEC_S_ENERGY);
+        double Ck = E, Qk = 1.0;
+        bool have_prev = false;
+        for (long long k = 0; k <= maxit; ++k) {
+            TRY(grad(u, nullptr, rg));
+            if (have_prev) TRY(Ops<T>::bbdots(g, w, u, up, rg, rgp, SL_D0, s));
+            PULL(ds);
+            if (ds == SBEC_ERR_DOMAIN) return SBEC_ERR_DOMAIN;
+            gn = sqrt(sc(SBEC_S_RGRAD_NORM2));
+            if (gn <= tol || k == maxit) return SBEC_OK;
+            double gam = 1e-3;
+            if (have_prev) {
+                const double sv = sc(SL_D0), vv = sc(SL_D0 + 1);
+                gam = vv > 0.0 ? fabs(sv) / vv : 1e-3;
+                gam = fmin(fmax(gam, 1e-10), 1e10);
+            }
+            const double slope = -gn * gn;
+            double t = gam, Ez = INFINITY;
+            for (int bt = 0; bt <= 10; ++bt) {
+                TRY(retract(u, rg, -t, z));
+                TRY(energy(z));
+                PULL(ds);
+                Ez = (ds == SBEC_ERR_DOMAIN) ? INFINITY : sc(SBEC_S_ENERGY);
+                if (Ez <= Ck + 1e-4 * t * slope) break;
+                t *= 0.2;
+            }
+            if (!isfinite(Ez)) return SBEC_ERR_DOMAIN;
+            void* tmp = up; up = u; u = z; z = tmp;
+            tmp = rgp; rgp = rg; rg = tmp;
+            have_prev = true;
+            E = Ez;
+            const double Qn = 0.85 * Qk + 1.0;
+            Ck = (0.85 * Qk * Ck + E) / Qn;
+            Qk = Qn;
+            ++st->rgbb_iters;
+        }
+        return SBEC_OK;
+    }
+
+    // ARNT from u (Algorithm 1, second loop)
+    int arnt(void*& u, void*& z, void* gE, void* rg, void* x, void* r, void* p, void* Hp, double tol,
+             long long maxit, double& E, double& gn) {
+        int ds;
+        TRY(energy(u));
+        PULL(ds);
+        E = sc(SBEC_S_ENERGY);
+        double sig_hat = 1.0, sig_floor = 0.0;
+        TRY(grad(u, gE, rg));
+        PULL(ds);
+        gn = sqrt(sc(SBEC_S_RGRAD_NORM2));
+        for (long long k = 0; k <= maxit; ++k) {
+            if (gn <= tol || k == maxit) break;
+            const double sigma = fmax(sig_hat * gn, sig_floor);
+            const int max_inner = gn > 1e-3 ? 100 : 300;
+            // ---- modified CG on Hess m_k [xi] = -grad m_k (Eq. prob-lsub) ----
+            TRY(lin(x, 0.0, rg, 0.0, nullptr));
+            TRY(lin(r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
+            TRY(lin(p, 1.0, r, 0.0, nullptr));
+            PULL(ds);
+            double rr = sc(SL_RRA);
+            const double stop = fmin(0.1, gn) * gn;
+            bool s_is_neg_rg = false, have_d = false;
+            double sig_est = -1.0;
+            if (rr > 0.0) {
+                for (int j = 0; j < max_inner; ++j) {
+                    const int rr_now = (j & 1) ? SL_RRB : SL_RRA, rr_next = (j & 1) ? SL_RRA : SL_RRB;
+                    TRY(hess(u, p, sigma, 1, Hp));
+                    TRY(Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, s));
+                    TRY(Ops<T>::ratio(w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s));
+                    TRY(lin(x, 1.0, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1));
+                    TRY(lin(r, 1.0, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, nullptr, rr_next));
+                    PULL(ds);
+                    ++st->inner_iters;
+                    const double kap = sc(SL_KAP), pp = sc(SL_KAP + 1), rrn = sc(rr_next);
+                    if (kap <= 1e-12 * pp) {
+                        sig_est = fabs(kap) / pp;
+                        if (j == 0) s_is_neg_rg = true;
+                        else if (kap < -1e-12 * pp) have_d = true;
+                        break;
+                    }
+                    if (sqrt(rrn) <= stop) break;
+                    TRY(lin(p, 1.0, r, rrn / rr, p));
+                    rr = rrn;
+                }
+            }
+            // ---- direction xi = s + tau d (Eq. xi), kept in x ----
+            if (s_is_neg_rg) {
+                TRY(lin(x, -1.0, rg, 0.0, nullptr));
+            } else if (have_d) {
+                TRY(Ops<T>::dot2(g, w, p, rg, p, Hp, SL_D0, s));
+                PULL(ds);
+                const double tau = sc(SL_D0) / sc(SL_D0 + 1);
+                TRY(lin(x, 1.0, x, tau, p));
+            }
+            TRY(Ops<T>::dot2(g, w, rg, x, nullptr, nullptr, SL_D0, s));
+            PULL(ds);
+            double slope = sc(SL_D0);
+            if (!(slope < 0.0) || !isfinite(slope)) {
+                TRY(lin(x, -1.0, rg, 0.0, nullptr));
+                slope = -gn * gn;
+            }
+            // ---- curvilinear search z = R_u(alpha0 delta^k xi) (Eq. tp1, tp2) ----
+            const double noise = 100.0 * kEps * fmax(1.0, fabs(E));
+            double t = 1.0, mz = INFINITY;
+            for (int bt = 0; bt <= 10; ++bt) {
+                TRY(retract(u, x, t, z));
+                TRY(lin(r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));     // dz = z - u
+                TRY(hess(u, r, 0.0, 0, Hp));                          // H dz (Euclidean)
+                TRY(Ops<T>::dot2(g, w, r, Hp, nullptr, nullptr, SL_MB, s));
+                PULL(ds);
+                mz = (ds == SBEC_ERR_DOMAIN) ? INFINITY
+                                             : sc(SL_MA) + 0.5 * sc(SL_MB) + 0.5 * sigma * sc(SL_MA + 1);
+                if (mz <= 1e-4 * t * slope || fabs(mz) <= noise) break;
+                t *= 0.2;
+            }
+            TRY(energy(z));
+            PULL(ds);
+            const double Ez = (ds == SBEC_ERR_DOMAIN) ? INFINITY : sc(SBEC_S_ENERGY);
+            double ratio;
+            if (fabs(mz) <= noise && fabs(Ez - E) <= noise) ratio = 1.0;
+            else ratio = (mz < 0.0 && isfinite(Ez)) ? (Ez - E) / mz : -1.0;
+            if (ratio >= 0.01) {
+                void* tmp = u; u = z; z = tmp;
+                E = Ez;
+                TRY(grad(u, gE, rg));
+                PULL(ds);
+                gn = sqrt(sc(SBEC_S_RGRAD_NORM2));
+                sig_hat *= (ratio >= 0.9) ? 0.2 : 1.0;
+            } else {
+                sig_hat *= 10.0;
+            }
+            sig_floor = sig_est >= 0.0 ? sig_est : 0.0;
+            ++st->outer_iters;
+            if (sig_hat > 1e20) break;
+        }
+        return SBEC_OK;
+    }
+
+    int run(void* Xdev) {
+        // fields: 0 u, 1 up, 2 z, 3 gE, 4 rg, 5 rgp, 6 x, 7 r, 8 p, 9 Hp
+        void *u = f[0], *up = f[1], *z = f[2], *rg = f[4], *rgp = f[5];
+        if (cudaMemcpyAsync(u, Xdev, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
+        int ds;
+        if (o.project_initial) {
+            TRY(retract(u, u, 0.0, u));
+            PULL(ds);
+            if (ds) return ds;
+        }
+        double E = 0.0, gn = INFINITY;
+        if (o.method == SBEC_RGBB) {
+            TRY(rgbb(u, up, z, rg, rgp, o.tol, o.maxit, E, gn));
+        } else {
+            TRY(rgbb(u, up, z, rg, rgp, fmax(o.tol, o.rgbb_tol), o.rgbb_maxit, E, gn));
+            if (gn > o.tol) {
+                // u and z are two distinct ones of fields 0..2 after RGBB's rotation
+                TRY(arnt(u, z, f[3], rg, f[6], f[7], f[8], f[9], o.tol, o.maxit, E, gn));
+            }
+        }
+        // final energy and gradient norm at the returned state
+        TRY(grad(u, nullptr, rg));
+        PULL(ds);
+        st->energy = sc(SBEC_S_ENERGY);
+        st->grad_norm = sqrt(sc(SBEC_S_RGRAD_NORM2));
+        st->converged = st->grad_norm <= o.tol;
+        if (cudaMemcpyAsync(Xdev, u, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SBEC_ERR_CUDA;
+        return st->converged ? SBEC_OK : SBEC_ERR_NOCONV;
+    }
+#undef TRY
+#undef PULL
+};
+
+}  // namespace
+
+extern "C" {
+
+void sbec_solve_defaults(sbec_solve_opts* o) {
+    if (!o) return;
+    o->method = SBEC_ARNT;
+    o->retraction = 1;
+    o->tol = 1e-6;
+    o->maxit = 10000;
+    o->rgbb_tol = 1e-2;
+    o->rgbb_maxit = 2000;
+    o->project_initial = 1;
+}
+
+int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes) {
+    if (!h || !bytes) return SBEC_ERR_ARG;
+    *bytes = 10 * h->field_bytes;
+    return SBEC_OK;
+}
+
+int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+               sbec_stats* stats) {
+    if (!h || !X || !workspace) return SBEC_ERR_ARG;
+    if (workspace_bytes < 10 * h->field_bytes || !sbec_is_device_ptr(workspace)) return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    if (o.retraction < 1 || o.retraction > 3 || !(o.tol > 0.0) || o.maxit < 0 || o.rgbb_maxit < 0) return SBEC_ERR_ARG;
+    sbec_stats local;
+    sbec_stats* st = stats ? stats : &local;
+    memset(st, 0, sizeof(*st));
+    // host arrays are staged through the handle's first staging field
+    const bool host = !sbec_is_device_ptr(X);
+    void* Xd = X;
+    if (host) {
+        Xd = h->stage[0];
+        if (cudaMemcpyAsync(Xd, X, h->field_bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+    }
+    int rc;
+    if (h->prob.precision == SBEC_FP64) {
+        Solver<double> S(h, o, workspace, st);
+        rc = S.run(Xd);
+    } else {
+        Solver<float> S(h, o, workspace, st);
+        rc = S.run(Xd);
+    }
+    h->last_grad_X = nullptr;
+    if (host && (rc == SBEC_OK || rc == SBEC_ERR_NOCONV)) {
+        if (cudaMemcpyAsync(X, Xd, h->field_bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -233,3 +233,52 @@ def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
     _check(_lib.sbec_energy_noalloc(ctypes.byref(pr), _ptr(V), _ptr(X), ctypes.byref(E), stream),
            "sbec_energy_noalloc")
     return E.value
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("retraction", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("rgbb_tol", ctypes.c_double), ("rgbb_maxit", ctypes.c_int),
+                ("project_initial", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("grad_norm", ctypes.c_double),
+                ("outer_iters", ctypes.c_longlong), ("inner_iters", ctypes.c_longlong),
+                ("rgbb_iters", ctypes.c_longlong), ("n_grad", ctypes.c_longlong),
+                ("n_energy", ctypes.c_longlong), ("n_hvp", ctypes.c_longlong),
+                ("converged", ctypes.c_int)]
+
+
+_lib.sbec_solve_defaults.argtypes = [ctypes.POINTER(SolveOpts)]
+_lib.sbec_solve_defaults.restype = None
+_lib.sbec_solve_workspace_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+_lib.sbec_solve_workspace_bytes.restype = _int
+_lib.sbec_solve.argtypes = [_vp, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.c_size_t, ctypes.POINTER(Stats)]
+_lib.sbec_solve.restype = _int
+ARNT, RGBB = 0, 1
+
+
+def _solve(self, X, method="arnt", retraction=1, tol=1e-8, maxit=10000, rgbb_tol=1e-2,
+           rgbb_maxit=2000, project=True, workspace=None):
+    """Ground state from X (overwritten) by sbec_solve; returns the stats as a dict.
+    Raises SbecError unless the tolerance was reached (status NOCONV included)."""
+    o = SolveOpts()
+    _lib.sbec_solve_defaults(ctypes.byref(o))
+    o.method = ARNT if method == "arnt" else RGBB
+    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
+    o.rgbb_tol, o.rgbb_maxit, o.project_initial = float(rgbb_tol), int(rgbb_maxit), int(bool(project))
+    nb = ctypes.c_size_t()
+    _check(_lib.sbec_solve_workspace_bytes(self._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
+    if workspace is None:
+        import torch
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    st = Stats()
+    rc = _lib.sbec_solve(self._h, _ptr(X), ctypes.byref(o), _ptr(workspace), nb.value, ctypes.byref(st))
+    out = {k: getattr(st, k) for k, _ in Stats._fields_}
+    out["status"] = rc
+    if rc not in (OK, ERR_NOCONV):
+        _check(rc, "sbec_solve")
+    return out
+
+
+Handle.solve = _solve

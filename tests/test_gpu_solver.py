@@ -1,0 +1,98 @@
+"""The GPU solver (sbec_solve: RGBB warm start + ARNT, Sec. 5 / Algorithm 1)
+against the oracle's solver and against the paper's printed energies: the
+ground-state energy matches to 1e-10 relative in FP64, the constraints hold
+to 1e-12 and the Riemannian gradient norm reaches the tolerance."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sbec_oracle as O  # noqa: E402
+from paper_1907_01194_gb300 import workloads as W  # noqa: E402
+from tests.oracle_helpers import paper_spin2_1d  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def _oracle_solve(w, X0, tol, method="arnt", retraction=1):
+    P = O.Problem(F=w.F, n=w.n, lo=w.lo, hi=w.hi, beta=w.beta, V=W.potential(w), M=w.M)
+    Xs, st, _ = O.solve(P, O.to_matrix(P, X0), O.SolveOptions(tol=tol, method=method,
+                                                             retraction=retraction))
+    return P, st
+
+
+def _constraints(w, Xf):
+    m = np.sum(np.abs(Xf.reshape(w.C, -1)) ** 2, axis=1)
+    ls = np.arange(w.F, -w.F - 1, -1)
+    return m.sum(), m @ ls
+
+
+CASES = [
+    (W.spin1_1d(), 1e-10),                                                  # 1D, spin-1
+    (W.Workload("s2_2d_32", F=2, n=(32, 32), lo=(-6.0, -6.0), hi=(6.0, 6.0),
+                beta=(60.0, 2.0, -3.0, 0.0), M=0.4, lattice_amp=3.0, lattice_k=math.pi / 2), 1e-9),
+    (W.Workload("s3_1d_128", F=3, n=(128,), lo=(-8.0,), hi=(8.0,),
+                beta=(80.0, -1.0, 4.0, 1.0), M=0.6), 1e-9),
+]
+
+
+@pytest.mark.parametrize("w,tol", CASES, ids=lambda c: getattr(c, "name", str(c)))
+def test_arnt_ground_state_matches_oracle(w, tol, dev):
+    from paper_1907_01194_gb300 import sbec
+    X0 = W.initial_fields(w)
+    X = torch.from_numpy(X0).to(dev)
+    with sbec.Handle.from_workload(w) as h:
+        st = h.solve(X, tol=tol)
+    P, ost = _oracle_solve(w, X0, tol)
+    assert st["converged"] and ost.converged
+    assert st["grad_norm"] <= tol
+    assert abs(st["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+    N, Mg = _constraints(w, X.cpu().numpy())
+    assert abs(N - 1) < 1e-12 and abs(Mg - w.M) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_rgbb_ground_state_matches_oracle(kind, dev):
+    from paper_1907_01194_gb300 import sbec
+    w = W.Workload("s1_1d_64", F=1, n=(64,), lo=(-8.0,), hi=(8.0,), beta=(30.0, -1.0, 0, 0), M=0.3)
+    X0 = W.initial_fields(w)
+    X = torch.from_numpy(X0).to(dev)
+    with sbec.Handle.from_workload(w) as h:
+        st = h.solve(X, method="rgbb", retraction=kind, tol=1e-7)
+    P, ost = _oracle_solve(w, X0, 1e-9)
+    assert st["converged"]
+    assert abs(st["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+
+
+def test_paper_spin2_1d_case_I_energy(dev):
+    # ten-digit value of the paper's Sec. 7.2 table (tests/golden/spin2_1d_energies.txt)
+    from paper_1907_01194_gb300 import sbec
+    P, X0m = paper_spin2_1d(1, 0.5)
+    w = W.Workload("paper_s2_1d_I", F=2, n=(256,), lo=(-8.0,), hi=(8.0,),
+                   beta=(130.6, -25.4, -125.3, 0.0), M=0.5, lattice_amp=25.0, lattice_k=math.pi / 4)
+    X = torch.from_numpy(O.to_fields(P, X0m)).to(dev)
+    with sbec.Handle.from_workload(w, V=P.V) as h:
+        st = h.solve(X, tol=1e-9)
+    assert st["converged"]
+    assert abs(st["energy"] - 10.3700300090) < 1e-9
+
+
+def test_host_array_solve_matches_device(dev):
+    from paper_1907_01194_gb300 import sbec
+    w = CASES[0][0]
+    X0 = W.initial_fields(w)
+    Xd = torch.from_numpy(X0).to(dev)
+    Xh = np.array(X0, copy=True)
+    with sbec.Handle.from_workload(w) as h:
+        a = h.solve(Xd, tol=1e-9)
+        b = h.solve(Xh, tol=1e-9)
+    assert a["energy"] == b["energy"] and a["n_hvp"] == b["n_hvp"]
+    assert np.array_equal(Xd.cpu().numpy(), Xh)
