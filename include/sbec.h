@@ -148,6 +148,15 @@ int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes);
 int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
                sbec_stats* stats);
 
+/* Mixed-precision solve with FP64 refinement: X (complex128, device) is cast to
+ * float, solved on h32 (precision SBEC_MIXED, same problem and stream as h64)
+ * to max(tol_mixed, opts->tol), cast back, projected on M and refined on h64
+ * (SBEC_FP64) to opts->tol.  Stats of both phases are returned.  workspace:
+ * device memory of at least sbec_solve_mixed_workspace_bytes. */
+int sbec_solve_mixed_workspace_bytes(const sbec_handle* h64, const sbec_handle* h32, size_t* bytes);
+int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_solve_opts* opts, double tol_mixed,
+                     void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64);
+
 /* Stream synchronisation; returns the first device-side error recorded since
  * the previous sbec_sync (and clears it), or SBEC_ERR_CUDA. */
 int sbec_sync(sbec_handle* h);

@@ -20,7 +20,8 @@
 //  * curvilinear search: alpha0 = 1, delta = 0.2, rho = 1e-4, at most 10
 //    reductions; m_k(z) is evaluated exactly with one Euclidean
 //    Hessian-vector product.  Below the rounding floor 100 eps max(1, |E|)
-//    of E the Armijo test and the ratio are taken as satisfied.
+//    of E (eps of the handle's precision) the Armijo test and the ratio are
+//    taken as satisfied.
 #include <math.h>
 #include <string.h>
 
@@ -203,7 +204,9 @@ struct Solver {
                 slope = -gn * gn;
             }
             // ---- curvilinear search z = R_u(alpha0 delta^k xi) (Eq. tp1, tp2) ----
-            const double noise = 100.0 * kEps * fmax(1.0, fabs(E));
+            // rounding floor of E: the energy's pointwise terms are summed from values
+            // of the handle's precision T
+            const double noise = 100.0 * (sizeof(T) == 8 ? kEps : 1.1920928955078125e-07) * fmax(1.0, fabs(E));
             double t = 1.0, mz = INFINITY;
             for (int bt = 0; bt <= 10; ++bt) {
                 TRY(retract(u, x, t, z));
@@ -327,6 +330,55 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
             return SBEC_ERR_CUDA;
     }
     return rc;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename TS, typename TD>
+__global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = TD(src[i]);
+}
+}  // namespace
+
+extern "C" {
+
+// Mixed form (FP32 FFT and pointwise arithmetic, FP64 reductions and scalars)
+// followed by an FP64 refinement from its result.
+int sbec_solve_mixed_workspace_bytes(const sbec_handle* h64, const sbec_handle* h32, size_t* bytes) {
+    if (!h64 || !h32 || !bytes) return SBEC_ERR_ARG;
+    *bytes = 10 * h64->field_bytes + 11 * h32->field_bytes;
+    return SBEC_OK;
+}
+
+int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_solve_opts* opts, double tol_mixed,
+                     void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64) {
+    if (!h64 || !h32 || !X || !workspace) return SBEC_ERR_ARG;
+    if (h64->prob.precision != SBEC_FP64 || h32->prob.precision != SBEC_MIXED) return SBEC_ERR_ARG;
+    if (h64->geom.G != h32->geom.G || h64->geom.C != h32->geom.C || h64->stream != h32->stream) return SBEC_ERR_ARG;
+    size_t need = 0;
+    sbec_solve_mixed_workspace_bytes(h64, h32, &need);
+    if (workspace_bytes < need || !sbec_is_device_ptr(X) || !sbec_is_device_ptr(workspace)) return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    char* base = static_cast<char*>(workspace);
+    void* ws64 = base;
+    void* X32 = base + 10 * h64->field_bytes;
+    void* ws32 = base + 10 * h64->field_bytes + h32->field_bytes;
+    const long long nreal = 2LL * h64->geom.C * h64->geom.G;
+    const int blocks = 4 * h64->work.num_sms;
+    k_cast<double, float><<<blocks, 256, 0, h64->stream>>>(static_cast<const double*>(X), static_cast<float*>(X32), nreal);
+    if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
+    sbec_solve_opts om = o;
+    om.tol = tol_mixed > o.tol ? tol_mixed : o.tol;
+    int rc = sbec_solve(h32, X32, &om, ws32, 10 * h32->field_bytes, st_mixed);
+    if (rc != SBEC_OK && rc != SBEC_ERR_NOCONV) return rc;
+    k_cast<float, double><<<blocks, 256, 0, h64->stream>>>(static_cast<const float*>(X32), static_cast<double*>(X), nreal);
+    if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
+    sbec_solve_opts of = o;
+    of.project_initial = 1;            // the float state is back on M to double precision
+    return sbec_solve(h64, X, &of, ws64, 10 * h64->field_bytes, st_fp64);
 }
 
 }  // extern "C"

@@ -282,3 +282,36 @@ def _solve(self, X, method="arnt", retraction=1, tol=1e-8, maxit=10000, rgbb_tol
 
 
 Handle.solve = _solve
+
+
+_lib.sbec_solve_mixed_workspace_bytes.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]
+_lib.sbec_solve_mixed_workspace_bytes.restype = _int
+_lib.sbec_solve_mixed.argtypes = [_vp, _vp, _vp, ctypes.POINTER(SolveOpts), _dbl, _vp, ctypes.c_size_t,
+                                  ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
+_lib.sbec_solve_mixed.restype = _int
+
+
+def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction=1, maxit=10000,
+                rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None):
+    """Mixed-precision solve on h32 then FP64 refinement on h64 (sbec_solve_mixed).
+    X: complex128 device tensor, overwritten.  Returns (stats_mixed, stats_fp64)."""
+    o = SolveOpts()
+    _lib.sbec_solve_defaults(ctypes.byref(o))
+    o.method = ARNT if method == "arnt" else RGBB
+    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
+    o.rgbb_tol, o.rgbb_maxit = float(rgbb_tol), int(rgbb_maxit)
+    nb = ctypes.c_size_t()
+    _check(_lib.sbec_solve_mixed_workspace_bytes(h64._h, h32._h, ctypes.byref(nb)),
+           "sbec_solve_mixed_workspace_bytes")
+    if workspace is None:
+        import torch
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    sm, sf = Stats(), Stats()
+    rc = _lib.sbec_solve_mixed(h64._h, h32._h, _ptr(X), ctypes.byref(o), float(tol_mixed), _ptr(workspace),
+                               nb.value, ctypes.byref(sm), ctypes.byref(sf))
+    if rc not in (OK, ERR_NOCONV):
+        _check(rc, "sbec_solve_mixed")
+    a = {k: getattr(sm, k) for k, _ in Stats._fields_}
+    b = {k: getattr(sf, k) for k, _ in Stats._fields_}
+    b["status"] = rc
+    return a, b
