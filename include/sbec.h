@@ -157,6 +157,20 @@ int sbec_solve_mixed_workspace_bytes(const sbec_handle* h64, const sbec_handle* 
 int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_solve_opts* opts, double tol_mixed,
                      void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64);
 
+/* Cascadic multigrid (Algorithm 1: solve on a coarse mesh, refine uniformly,
+ * repeat).  sbec_prolongate maps a state of handle hc to the finer handle hf
+ * (same spin, box, precision and stream; n_f >= n_c per axis): the coarse
+ * spectrum is zero-padded (the coarse Nyquist coefficient split evenly between
+ * +-n_c/2), transformed back, rescaled to keep X = sqrt(dV) phi and put on M
+ * with R1 (Lemma 5.1).  sbec_solve_cascadic solves on levels[0..nlevels-1]
+ * (coarse to fine) with X[j] the caller's state array of level j (X[0] holds
+ * the initial data); coarse levels stop at max(tol_coarse, opts->tol)
+ * (Sec. 7.1: 1e-5), the finest at opts->tol; stats are those of the finest
+ * level.  workspace: at least sbec_solve_workspace_bytes of the finest handle. */
+int sbec_prolongate(sbec_handle* hc, const void* Xc, sbec_handle* hf, void* Xf);
+int sbec_solve_cascadic(sbec_handle* const* levels, int nlevels, void* const* X, const sbec_solve_opts* opts,
+                        double tol_coarse, void* workspace, size_t workspace_bytes, sbec_stats* stats);
+
 /* Stream synchronisation; returns the first device-side error recorded since
  * the previous sbec_sync (and clears it), or SBEC_ERR_CUDA. */
 int sbec_sync(sbec_handle* h);

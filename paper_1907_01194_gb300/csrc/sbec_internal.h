@@ -40,7 +40,7 @@ struct Geom {
 enum KernelId {
     K_X_FWD, K_X_FWD_EPW, K_X_INV_GRAD, K_X_INV_HESS, K_X_FULL_GRAD, K_X_FULL_ENERGY, K_X_FULL_HESS,
     K_S_FWD, K_S_INV, K_S_K2, K_S_PARSEVAL, K_DOT, K_PROJ, K_RETW, K_SCALE, K_FIN, K_RSOLVE, K_TABLES,
-    K_LIN, K_PROLONG, K_COUNT
+    K_LIN, K_PROLONG, K_X_INV, K_COUNT
 };
 
 // Launch bookkeeping of one handle: every library kernel launch is counted;
@@ -108,6 +108,8 @@ template <typename T> struct Ops {
                        void* HZ, cudaStream_t s);
     static int retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind,
                        void* out, cudaStream_t s);
+    static int prolongate(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf,
+                          void* Xf, cudaStream_t s);
     static int init_tables(Geom& g, void* tw_storage, cudaStream_t s);
     static int harmonic_potential(const Geom& g, void* V, const double* lo, const double* hi, cudaStream_t s);
     static int convert_potential(const Geom& g, void* V, const double* Vd, cudaStream_t s);

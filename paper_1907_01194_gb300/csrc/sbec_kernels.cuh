@@ -34,7 +34,8 @@ enum XMode {
     X_INV_HESS = 3,    // inverse x-FFT + Hessian epilogue, partials n_l, t_l
     X_FULL_GRAD = 4,   // 1D: fwd, |k|^2/G, inv, gradient epilogue
     X_FULL_ENERGY = 5, // 1D: pointwise energy + fwd + Parseval
-    X_FULL_HESS = 6    // 1D: fwd, |k|^2/G, inv, Hessian epilogue
+    X_FULL_HESS = 6,   // 1D: fwd, |k|^2/G, inv, Hessian epilogue
+    X_INV = 7          // inverse x-FFT of every row, stored
 };
 
 enum SMode { S_FWD = 0, S_INV = 1, S_K2 = 2, S_PARSEVAL = 3 };
@@ -105,7 +106,8 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         __syncthreads();
     }
 
-    const bool fwd = (MODE == X_FWD || MODE == X_FWD_EPW || MODE >= X_FULL_GRAD);
+    const bool fwd = (MODE == X_FWD || MODE == X_FWD_EPW || MODE == X_FULL_GRAD || MODE == X_FULL_ENERGY ||
+                      MODE == X_FULL_HESS);
     if (fwd) fft_pencils<T2, false, ITEMS>(buf, logn, P, n, 1, tw, tid, nth);
 
     if (MODE == X_FULL_ENERGY) {
@@ -122,10 +124,11 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         }
         __syncthreads();
     }
-    const bool inv = (MODE == X_INV_GRAD || MODE == X_INV_HESS || MODE == X_FULL_GRAD || MODE == X_FULL_HESS);
+    const bool inv = (MODE == X_INV_GRAD || MODE == X_INV_HESS || MODE == X_FULL_GRAD || MODE == X_FULL_HESS ||
+                      MODE == X_INV);
     if (inv) fft_pencils<T2, true, ITEMS>(buf, logn, P, n, 1, tw, tid, nth);
 
-    if (MODE == X_FWD || MODE == X_FWD_EPW) {
+    if (MODE == X_FWD || MODE == X_FWD_EPW || MODE == X_INV) {
         T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
         for (int idx = tid; idx < P * n; idx += nth) {
             const int p = idx >> logn, e = idx & (n - 1);
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         }
     }
 
-    if (MODE != X_FWD) block_reduce_store<NQ>(acc, a.partials, a.nblk, blockIdx.x);
+    if (MODE != X_FWD && MODE != X_INV) block_reduce_store<NQ>(acc, a.partials, a.nblk, blockIdx.x);
 }
 
 struct SArgs {
@@ -657,6 +660,42 @@ static __global__ void k_ratio(double* scal, int dst, int num, int den, int guar
 }
 
 // ---------------------------------------------------------------------------
+// Cascadic prolongation (Algorithm 1, "refine uniformly"): the coarse spectrum
+// is zero-padded to the fine grid; the coarse Nyquist coefficient (p = -n_c/2)
+// is split evenly between p = +-n_c/2 of the fine grid on every refined axis.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pad_map(int i_f, int nc, int nf, double* wgt) {
+    if (nc == nf) { *wgt = 1.0; return i_f; }
+    const int h = nc >> 1;
+    if (i_f < h) { *wgt = 1.0; return i_f; }
+    if (i_f == h || i_f == nf - h) { *wgt = 0.5; return h; }
+    if (i_f > nf - h) { *wgt = 1.0; return i_f - nf + nc; }
+    *wgt = 0.0;
+    return 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pad(const void* srcp, void* dstp, int C, int ncx, int ncy, int ncz,
+                                             int nfx, int nfy, int nfz, double scale) {
+    using T2 = typename C2<T>::t;
+    const T2* __restrict__ src = reinterpret_cast<const T2*>(srcp);
+    T2* __restrict__ dst = reinterpret_cast<T2*>(dstp);
+    const long long Gf = (long long)nfx * nfy * nfz, Gc = (long long)ncx * ncy * ncz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)C * Gf;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i / Gf);
+        const long long p = i - (long long)c * Gf;
+        const int ix = (int)(p % nfx), iy = (int)((p / nfx) % nfy), iz = (int)(p / ((long long)nfx * nfy));
+        double wx, wy, wz;
+        const int jx = pad_map(ix, ncx, nfx, &wx), jy = pad_map(iy, ncy, nfy, &wy), jz = pad_map(iz, ncz, nfz, &wz);
+        const double wgt = wx * wy * wz * scale;
+        T2 v = mk<T2>(0, 0);
+        if (wgt != 0.0) v = cscale(src[(long long)c * Gc + ((long long)jz * ncy + jy) * ncx + jx], T(wgt));
+        dst[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Tables
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -773,7 +812,7 @@ template <int MODE> struct XKid {
     static constexpr int v = MODE == X_FWD ? K_X_FWD : MODE == X_FWD_EPW ? K_X_FWD_EPW
                            : MODE == X_INV_GRAD ? K_X_INV_GRAD : MODE == X_INV_HESS ? K_X_INV_HESS
                            : MODE == X_FULL_GRAD ? K_X_FULL_GRAD : MODE == X_FULL_ENERGY ? K_X_FULL_ENERGY
-                           : K_X_FULL_HESS;
+                           : MODE == X_FULL_HESS ? K_X_FULL_HESS : K_X_INV;
 };
 template <int MODE> struct SKid {
     static constexpr int v = MODE == S_FWD ? K_S_FWD : MODE == S_INV ? K_S_INV : MODE == S_K2 ? K_S_K2 : K_S_PARSEVAL;
@@ -1059,6 +1098,48 @@ template <typename T>
 int Ops<T>::ratio(const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps, cudaStream_t s) {
     SBEC_LAUNCH(K_FIN, k_ratio, 1, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps);
     return SBEC_OK;
+}
+
+template <typename T, int F>
+static int prolongate_F(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf, void* Xf,
+                        cudaStream_t s) {
+    // coarse forward transform into the coarse scratch
+    {
+        const Work& w = wc;
+        const XCfg c = xcfg<T>(gc);
+        int st = launch_x<T, F, X_FWD>(c, xargs<T>(gc, c, Xc, wc.work, nullptr), w, s);
+        if (st) return st;
+        for (int ax = 1; ax < gc.dim; ++ax) {
+            const SCfg sc = scfg<T>(gc, ax, wc.num_sms);
+            st = launch_s<T, S_FWD>(sc, sargs<T>(gc, sc, ax, wc.work, wc.work, nullptr), w, s);
+            if (st) return st;
+        }
+    }
+    const Work& w = wf;
+    // zero-pad into the fine scratch; 1/G_c undoes the coarse forward DFT's scale on
+    // inversion and sqrt(dV_f / dV_c) keeps X = sqrt(dV) phi
+    const double scale = sqrt(gf.dV / gc.dV) / (double)gc.G;
+    SBEC_LAUNCH(K_PROLONG, k_pad<T>, elem_blocks((long long)gf.C * gf.G, wf.num_sms), 256, wc.work, wf.work, gc.C,
+                gc.n[0], gc.n[1], gc.n[2], gf.n[0], gf.n[1], gf.n[2], scale);
+    for (int ax = gf.dim - 1; ax >= 1; --ax) {
+        const SCfg sc = scfg<T>(gf, ax, wf.num_sms);
+        int st = launch_s<T, S_INV>(sc, sargs<T>(gf, sc, ax, wf.work, wf.work, nullptr), w, s);
+        if (st) return st;
+    }
+    const XCfg c = xcfg<T>(gf);
+    int st = launch_x<T, F, X_INV>(c, xargs<T>(gf, c, wf.work, Xf, nullptr), w, s);
+    if (st) return st;
+    // back onto M with the projective retraction (Lemma 5.1)
+    return retract_F<T, F>(gf, wf, Xf, Xf, 0.0, 1, Xf, s);
+}
+
+template <typename T>
+int Ops<T>::prolongate(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf, void* Xf,
+                       cudaStream_t s) {
+    const Geom& g = gf;
+#define P_(F) prolongate_F<T, F>(gc, wc, Xc, gf, wf, Xf, s)
+    SBEC_DISPATCH_F(P_)
+#undef P_
 }
 
 template <typename T>

@@ -381,4 +381,54 @@ int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_sol
     return sbec_solve(h64, X, &of, ws64, 10 * h64->field_bytes, st_fp64);
 }
 
+// Cascadic multigrid (Algorithm 1, outer loop over meshes).
+int sbec_prolongate(sbec_handle* hc, const void* Xc, sbec_handle* hf, void* Xf) {
+    if (!hc || !hf || !Xc || !Xf) return SBEC_ERR_ARG;
+    const sbec_problem &a = hc->prob, &b = hf->prob;
+    if (a.F != b.F || a.dim != b.dim || a.precision != b.precision || hc->stream != hf->stream) return SBEC_ERR_ARG;
+    for (int ax = 0; ax < a.dim; ++ax)
+        if (b.n[ax] < a.n[ax] || a.lo[ax] != b.lo[ax] || a.hi[ax] != b.hi[ax]) return SBEC_ERR_ARG;
+    bool host = false;
+    const void* Xcd = Xc;
+    if (!sbec_is_device_ptr(Xc)) {
+        host = true;
+        if (cudaMemcpyAsync(hc->stage[0], Xc, hc->field_bytes, cudaMemcpyHostToDevice, hc->stream) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+        Xcd = hc->stage[0];
+    }
+    void* Xfd = Xf;
+    if (!sbec_is_device_ptr(Xf)) { host = true; Xfd = hf->stage[2]; }
+    const int st = a.precision == SBEC_FP64
+                       ? sbec::Ops<double>::prolongate(hc->geom, hc->work, Xcd, hf->geom, hf->work, Xfd, hf->stream)
+                       : sbec::Ops<float>::prolongate(hc->geom, hc->work, Xcd, hf->geom, hf->work, Xfd, hf->stream);
+    if (st) return st;
+    if (Xfd != Xf && cudaMemcpyAsync(Xf, Xfd, hf->field_bytes, cudaMemcpyDeviceToHost, hf->stream) != cudaSuccess)
+        return SBEC_ERR_CUDA;
+    hf->last_grad_X = nullptr;
+    return host ? sbec_read_scalars(hf) : SBEC_OK;
+}
+
+int sbec_solve_cascadic(sbec_handle* const* levels, int nlevels, void* const* X, const sbec_solve_opts* opts,
+                        double tol_coarse, void* workspace, size_t workspace_bytes, sbec_stats* stats) {
+    if (!levels || !X || nlevels < 1) return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    int rc = SBEC_OK;
+    for (int j = 0; j < nlevels; ++j) {
+        if (!levels[j] || !X[j]) return SBEC_ERR_ARG;
+        if (j > 0) {
+            rc = sbec_prolongate(levels[j - 1], X[j - 1], levels[j], X[j]);
+            if (rc) return rc;
+        }
+        sbec_solve_opts oj = o;
+        const bool finest = (j == nlevels - 1);
+        oj.tol = finest ? o.tol : (tol_coarse > o.tol ? tol_coarse : o.tol);
+        oj.project_initial = (j == 0) ? o.project_initial : 0;     // the prolongation ends with R1
+        sbec_stats local;
+        rc = sbec_solve(levels[j], X[j], &oj, workspace, workspace_bytes, finest && stats ? stats : &local);
+        if (rc != SBEC_OK && !(rc == SBEC_ERR_NOCONV && !finest)) return rc;
+    }
+    return rc;
+}
+
 }  // extern "C"

@@ -315,3 +315,41 @@ def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction
     b = {k: getattr(sf, k) for k, _ in Stats._fields_}
     b["status"] = rc
     return a, b
+
+
+_lib.sbec_prolongate.argtypes = [_vp, _vp, _vp, _vp]
+_lib.sbec_prolongate.restype = _int
+_lib.sbec_solve_cascadic.argtypes = [ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp), ctypes.POINTER(SolveOpts),
+                                     _dbl, _vp, ctypes.c_size_t, ctypes.POINTER(Stats)]
+_lib.sbec_solve_cascadic.restype = _int
+
+
+def prolongate(hc, Xc, hf, Xf):
+    """Cascadic prolongation of Xc (handle hc) to Xf (finer handle hf), sbec_prolongate."""
+    _check(_lib.sbec_prolongate(hc._h, _ptr(Xc), hf._h, _ptr(Xf)), "sbec_prolongate")
+
+
+def solve_cascadic(handles, states, tol=1e-8, tol_coarse=1e-5, method="arnt", retraction=1, maxit=10000,
+                   rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None):
+    """sbec_solve_cascadic over handles (coarse to fine); states[j] is level j's array
+    (states[0] holds the initial data, the finest receives the ground state)."""
+    o = SolveOpts()
+    _lib.sbec_solve_defaults(ctypes.byref(o))
+    o.method = ARNT if method == "arnt" else RGBB
+    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
+    o.rgbb_tol, o.rgbb_maxit = float(rgbb_tol), int(rgbb_maxit)
+    nb = ctypes.c_size_t()
+    _check(_lib.sbec_solve_workspace_bytes(handles[-1]._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
+    if workspace is None:
+        import torch
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    hs = (_vp * len(handles))(*[h._h for h in handles])
+    xs = (_vp * len(states))(*[_ptr(x) for x in states])
+    st = Stats()
+    rc = _lib.sbec_solve_cascadic(hs, len(handles), xs, ctypes.byref(o), float(tol_coarse), _ptr(workspace),
+                                  nb.value, ctypes.byref(st))
+    if rc not in (OK, ERR_NOCONV):
+        _check(rc, "sbec_solve_cascadic")
+    out = {k: getattr(st, k) for k, _ in Stats._fields_}
+    out["status"] = rc
+    return out
