@@ -77,6 +77,16 @@ typedef struct sbec_handle sbec_handle;
 int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sbec_handle** out);
 int sbec_destroy(sbec_handle* h);
 
+/* Batch handle: `count` problems that share F, dim, n, box, p, q and precision
+ * and differ in beta and M.  Arrays of every call are then [count][C][G] (the
+ * instances back to back, each in the state layout), V is [count][G] doubles or
+ * NULL (harmonic), and host scalar outputs (E, rgrad_norm) receive `count`
+ * values.  Every kernel launch covers all instances: blocks map to (instance,
+ * tile) pairs, reductions and scalars are per instance. */
+int sbec_create_batch(const sbec_problem* probs, int count, const double* V, void* cuda_stream,
+                      sbec_handle** out);
+int sbec_batch_size(const sbec_handle* h);
+
 /* E_h(X), Eq. (3.7) with h -> dV.  E: host pointer or NULL (then the value is
  * left in the scalar block, slot SBEC_S_ENERGY). */
 int sbec_energy(sbec_handle* h, const void* X, double* E);

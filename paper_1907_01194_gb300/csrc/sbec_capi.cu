@@ -53,14 +53,18 @@ bool is_device_ptr(const void* p) {
     } while (0)
 
 int read_scalars(sbec_handle* h) {
-    TRY_CUDA(cudaMemcpyAsync(h->h_scal, h->work.scal, sbec::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
-                             h->stream));
+    const size_t n = (size_t)h->B * sbec::S_COUNT;
+    TRY_CUDA(cudaMemcpyAsync(h->h_scal, h->work.scal, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     TRY_CUDA(cudaStreamSynchronize(h->stream));
-    const int st = (int)h->h_scal[SBEC_S_STATUS];
+    int st = 0;
+    for (int b = 0; b < h->B; ++b) {
+        double& v = h->h_scal[(size_t)b * sbec::S_COUNT + SBEC_S_STATUS];
+        if (v != 0.0 && st == 0) st = (int)v;
+    }
     if (st != 0) {
-        const double zero = 0.0;
-        TRY_CUDA(cudaMemcpyAsync(h->work.scal + SBEC_S_STATUS, &zero, sizeof(double), cudaMemcpyHostToDevice,
-                                 h->stream));
+        // clear every instance's status: write the (now synchronised) block back with zeros there
+        for (int b = 0; b < h->B; ++b) h->h_scal[(size_t)b * sbec::S_COUNT + SBEC_S_STATUS] = 0.0;
+        TRY_CUDA(cudaMemcpyAsync(h->work.scal, h->h_scal, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         TRY_CUDA(cudaStreamSynchronize(h->stream));
     }
     return st;
@@ -106,6 +110,8 @@ void free_handle(sbec_handle* h) {
     cudaFree(h->work.partA);
     cudaFree(h->work.partB);
     cudaFree(h->work.scal);
+    cudaFree(h->d_ppb);
+    cudaFree(h->d_Mb);
     for (int i = 0; i < 3; ++i) cudaFree(h->stage[i]);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->prof.ev) {
@@ -133,13 +139,18 @@ const char* sbec_status_string(int s) {
     }
 }
 
-int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sbec_handle** out) {
-    if (!prob || !out) return SBEC_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// one problem (B = 1) or a batch of B problems that share spin, grid, box, Zeeman
+// terms and precision and differ in beta and M
+int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_stream, sbec_handle** out) {
+    if (!probs || !out || B < 1) return SBEC_ERR_ARG;
     *out = nullptr;
-    const sbec_problem& P = *prob;
+    const sbec_problem& P = probs[0];
     if (P.F < 1 || P.F > 3 || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
     if (P.precision != SBEC_FP64 && P.precision != SBEC_MIXED) return SBEC_ERR_ARG;
-    if (!(fabs(P.M) < (double)P.F)) return SBEC_ERR_ARG;
     for (int ax = 0; ax < 3; ++ax) {
         if (ax < P.dim) {
             if (!is_pow2(P.n[ax]) || P.n[ax] < 2 || P.n[ax] > 1024) return SBEC_ERR_ARG;
@@ -148,9 +159,17 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
             return SBEC_ERR_ARG;
         }
     }
+    for (int b = 0; b < B; ++b) {
+        const sbec_problem& Q = probs[b];
+        if (!(fabs(Q.M) < (double)P.F)) return SBEC_ERR_ARG;
+        if (Q.F != P.F || Q.dim != P.dim || Q.precision != P.precision || Q.p != P.p || Q.q != P.q) return SBEC_ERR_ARG;
+        for (int ax = 0; ax < 3; ++ax)
+            if (Q.n[ax] != P.n[ax] || Q.lo[ax] != P.lo[ax] || Q.hi[ax] != P.hi[ax]) return SBEC_ERR_ARG;
+    }
     sbec_handle* h = (sbec_handle*)calloc(1, sizeof(sbec_handle));
     if (!h) return SBEC_ERR_CUDA;
     h->prob = P;
+    h->B = B;
     h->stream = (cudaStream_t)cuda_stream;
     h->work.prof = &h->prof;
     if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return SBEC_ERR_CUDA; }
@@ -160,6 +179,7 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
 
     sbec::Geom& g = h->geom;
     g.F = P.F; g.C = 2 * P.F + 1; g.dim = P.dim;
+    g.B = B;
     double dV = 1.0;
     for (int ax = 0; ax < 3; ++ax) {
         g.n[ax] = P.n[ax];
@@ -174,35 +194,53 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
         const double l = (double)(P.F - i);
         g.bz[i] = (i < g.C) ? (-P.p * l + P.q * l * l) : 0.0;
     }
-    const double b0 = P.beta[0], b1 = P.beta[1];
-    const double b2 = P.F >= 2 ? P.beta[2] : 0.0, b3 = P.F == 3 ? P.beta[3] : 0.0;
-    g.g0 = 2 * b0 / dV; g.g1 = 2 * b1 / dV; g.g2 = 2 * b2 / dV; g.g3 = 2 * b3 / dV;
-    g.e0 = b0 / (2 * dV); g.e1 = b1 / (2 * dV); g.e2 = b2 / (2 * dV); g.e3 = b3 / (2 * dV);
+    // point parameters: beta_i / (2 dV) (energy) and 2 beta_i / dV (gradient, Hessian)
+    auto params = [&](const sbec_problem& Q, sbec::PointParams& pp) {
+        const double b0 = Q.beta[0], b1 = Q.beta[1];
+        const double b2 = Q.F >= 2 ? Q.beta[2] : 0.0, b3 = Q.F == 3 ? Q.beta[3] : 0.0;
+        for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
+        pp.g0 = 2 * b0 / dV; pp.g1 = 2 * b1 / dV; pp.g2 = 2 * b2 / dV; pp.g3 = 2 * b3 / dV;
+        pp.e0 = b0 / (2 * dV); pp.e1 = b1 / (2 * dV); pp.e2 = b2 / (2 * dV); pp.e3 = b3 / (2 * dV);
+    };
+    sbec::PointParams pp0;
+    params(P, pp0);
+    g.g0 = pp0.g0; g.g1 = pp0.g1; g.g2 = pp0.g2; g.g3 = pp0.g3;
+    g.e0 = pp0.e0; g.e1 = pp0.e1; g.e2 = pp0.e2; g.e3 = pp0.e3;
 
     const bool dbl = P.precision == SBEC_FP64;
     h->elem = dbl ? 2 * sizeof(double) : 2 * sizeof(float);
-    h->field_bytes = (size_t)g.C * (size_t)g.G * h->elem;
+    h->field_bytes = (size_t)B * (size_t)g.C * (size_t)g.G * h->elem;
     const size_t real_bytes = dbl ? sizeof(double) : sizeof(float);
     const size_t ntw = (size_t)P.n[0] + P.n[1] + P.n[2];
     const size_t part = dbl ? sbec::Ops<double>::partials_needed(g, h->work.num_sms)
                             : sbec::Ops<float>::partials_needed(g, h->work.num_sms);
     h->work.part_cap = part;
+    const size_t nscal = (size_t)B * sbec::S_COUNT;
 
     bool ok = true;
     ok = ok && cudaMalloc(&h->d_tw, ntw * h->elem) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->d_lam2, ntw * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc(&h->d_V, (size_t)g.G * real_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->d_V, (size_t)B * g.G * real_bytes) == cudaSuccess;
     ok = ok && cudaMalloc(&h->work.work, h->field_bytes) == cudaSuccess;
     ok = ok && cudaMalloc(&h->work.work2, h->field_bytes) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->work.partA, part * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->work.partB, part * sizeof(double)) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->work.scal, sbec::S_COUNT * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->work.scal, nscal * sizeof(double)) == cudaSuccess;
     for (int i = 0; i < 3; ++i) ok = ok && cudaMalloc(&h->stage[i], h->field_bytes) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&h->h_scal, sbec::S_COUNT * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&h->h_scal, nscal * sizeof(double)) == cudaSuccess;
+    if (ok && B > 1) {
+        ok = cudaMalloc(&h->d_ppb, (size_t)B * sizeof(sbec::PointParams)) == cudaSuccess &&
+             cudaMalloc((void**)&h->d_Mb, (size_t)B * sizeof(double)) == cudaSuccess;
+    }
     if (!ok) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }
 
-    // lambda_p^2 = (2 pi p / (b - a))^2 with p the signed DFT frequency (Eq. 3.6)
-    double* lam = (double*)malloc(ntw * sizeof(double));
+    // lambda_p^2 = (2 pi p / (b - a))^2 with p the signed DFT frequency (Eq. 3.6);
+    // per-instance parameters of a batch
+    const size_t host_bytes = ntw * sizeof(double) +
+                              (B > 1 ? (size_t)B * (sizeof(sbec::PointParams) + sizeof(double)) : 0);
+    char* hostbuf = (char*)malloc(host_bytes);
+    if (!hostbuf) { free_handle(h); return SBEC_ERR_CUDA; }
+    double* lam = (double*)hostbuf;
     size_t off = 0;
     for (int ax = 0; ax < 3; ++ax) {
         const int n = P.n[ax];
@@ -216,10 +254,20 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
         off += n;
     }
     cudaError_t ce = cudaMemcpyAsync(h->d_lam2, lam, ntw * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (B > 1 && ce == cudaSuccess) {
+        sbec::PointParams* ppb = (sbec::PointParams*)(hostbuf + ntw * sizeof(double));
+        double* Mb = (double*)(ppb + B);
+        for (int b = 0; b < B; ++b) { params(probs[b], ppb[b]); Mb[b] = probs[b].M; }
+        ce = cudaMemcpyAsync(h->d_ppb, ppb, (size_t)B * sizeof(sbec::PointParams), cudaMemcpyHostToDevice, h->stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(h->d_Mb, Mb, (size_t)B * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        g.ppb = h->d_ppb;
+        g.Mb = h->d_Mb;
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
-    free(lam);
+    free(hostbuf);
     if (ce != cudaSuccess) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }
-    if (cudaMemsetAsync(h->work.scal, 0, sbec::S_COUNT * sizeof(double), h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->work.scal, 0, nscal * sizeof(double), h->stream) != cudaSuccess) {
         free_handle(h);
         return SBEC_ERR_CUDA;
     }
@@ -227,22 +275,21 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
     g.V = h->d_V;
     int st = dbl ? sbec::Ops<double>::init_tables(g, h->d_tw, h->stream)
                  : sbec::Ops<float>::init_tables(g, h->d_tw, h->stream);
-    if (st == SBEC_OK) {
+    const double* Vd = V;
+    if (st == SBEC_OK && V != nullptr && !is_device_ptr(V)) {
+        // the caller's potential goes through a staging field (B G doubles fit in it)
+        if (cudaMemcpyAsync(h->stage[0], V, (size_t)B * g.G * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess) st = SBEC_ERR_CUDA;
+        Vd = (const double*)h->stage[0];
+    }
+    for (int b = 0; b < B && st == SBEC_OK; ++b) {
+        void* Vb = (char*)h->d_V + (size_t)b * g.G * real_bytes;
         if (V == nullptr) {
-            st = dbl ? sbec::Ops<double>::harmonic_potential(g, h->d_V, P.lo, P.hi, h->stream)
-                     : sbec::Ops<float>::harmonic_potential(g, h->d_V, P.lo, P.hi, h->stream);
+            st = dbl ? sbec::Ops<double>::harmonic_potential(g, Vb, P.lo, P.hi, h->stream)
+                     : sbec::Ops<float>::harmonic_potential(g, Vb, P.lo, P.hi, h->stream);
         } else {
-            // copy the caller's potential (host or device) through a staging field
-            const double* Vd = V;
-            void* tmp = h->stage[0];
-            if (!is_device_ptr(V)) {
-                if (cudaMemcpyAsync(tmp, V, (size_t)g.G * sizeof(double), cudaMemcpyHostToDevice, h->stream) !=
-                    cudaSuccess) st = SBEC_ERR_CUDA;
-                Vd = (const double*)tmp;
-            }
-            if (st == SBEC_OK)
-                st = dbl ? sbec::Ops<double>::convert_potential(g, h->d_V, Vd, h->stream)
-                         : sbec::Ops<float>::convert_potential(g, h->d_V, Vd, h->stream);
+            st = dbl ? sbec::Ops<double>::convert_potential(g, Vb, Vd + (size_t)b * g.G, h->stream)
+                     : sbec::Ops<float>::convert_potential(g, Vb, Vd + (size_t)b * g.G, h->stream);
         }
     }
     if (st == SBEC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = SBEC_ERR_CUDA;
@@ -250,6 +297,20 @@ int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sb
     *out = h;
     return SBEC_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+int sbec_create(const sbec_problem* prob, const double* V, void* cuda_stream, sbec_handle** out) {
+    return create_impl(prob, 1, V, cuda_stream, out);
+}
+
+int sbec_create_batch(const sbec_problem* probs, int count, const double* V, void* cuda_stream, sbec_handle** out) {
+    return create_impl(probs, count, V, cuda_stream, out);
+}
+
+int sbec_batch_size(const sbec_handle* h) { return h ? h->B : 0; }
 
 int sbec_destroy(sbec_handle* h) {
     if (!h) return SBEC_ERR_ARG;
@@ -325,7 +386,8 @@ int sbec_energy(sbec_handle* h, const void* X, double* E) {
     if (st) return st;
     if (E || host) {
         st = read_scalars(h);
-        if (E) *E = h->h_scal[SBEC_S_ENERGY];
+        if (E)
+            for (int b = 0; b < h->B; ++b) E[b] = h->h_scal[(size_t)b * sbec::S_COUNT + SBEC_S_ENERGY];
     }
     return st;
 }
@@ -347,8 +409,11 @@ int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* 
     if ((st = copy_back(h, G_riem, gr))) return st;
     if (E || rgrad_norm || host) {
         st = read_scalars(h);
-        if (E) *E = h->h_scal[SBEC_S_ENERGY];
-        if (rgrad_norm) *rgrad_norm = sqrt(h->h_scal[SBEC_S_RGRAD_NORM2]);
+        for (int b = 0; b < h->B; ++b) {
+            const double* sc = h->h_scal + (size_t)b * sbec::S_COUNT;
+            if (E) E[b] = sc[SBEC_S_ENERGY];
+            if (rgrad_norm) rgrad_norm[b] = sqrt(sc[SBEC_S_RGRAD_NORM2]);
+        }
     }
     return st;
 }

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sbec_internal.h"
+
 namespace sbec {
 
 template <typename T> struct C2;
@@ -234,12 +236,6 @@ __device__ __forceinline__ constexpr double qnt_entry(int k, int i) {
 }
 __device__ __forceinline__ constexpr int qnt_l(int k) { return 2 - k; }
 
-// Physical parameters handed to the pointwise code (precomputed on the host).
-struct PointParams {
-    double bz[7];       // Zeeman diagonal b_l = -p l + q l^2 per component index
-    double g0, g1, g2, g3;  // 2 beta_i / dV (gradient / Hessian prefactors)
-    double e0, e1, e2, e3;  // beta_i / (2 dV) (energy prefactors)
-};
 
 // Densities at one grid point (Sec. 3): rho, F_z, F_+, A00, A_{2l}.
 template <int F, typename T2>

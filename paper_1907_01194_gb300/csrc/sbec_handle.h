@@ -22,6 +22,9 @@ struct sbec_handle {
     double* h_scal;       // pinned mirror of the scalar block
     const void* last_grad_X;
     sbec::Prof prof;
+    int B;                // instances of a batch handle (1 for sbec_create)
+    void* d_ppb;          // per-instance PointParams (batch handles)
+    double* d_Mb;         // per-instance magnetisations (batch handles)
 };
 
 // helpers of the C-ABI translation unit used by the solver

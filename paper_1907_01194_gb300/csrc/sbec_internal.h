@@ -22,6 +22,13 @@ enum {
     S_COUNT = 128
 };
 
+// Physical parameters handed to the pointwise code (precomputed on the host).
+struct PointParams {
+    double bz[7];           // Zeeman diagonal b_l = -p l + q l^2 per component index
+    double g0, g1, g2, g3;  // 2 beta_i / dV (gradient / Hessian prefactors)
+    double e0, e1, e2, e3;  // beta_i / (2 dV) (energy prefactors)
+};
+
 // Geometry and parameters of one problem as the kernels see it.
 struct Geom {
     int F, C, dim;
@@ -34,6 +41,11 @@ struct Geom {
     const void* V;            // potential, T
     double bz[7];
     double g0, g1, g2, g3, e0, e1, e2, e3;
+    // batches: B instances of one shape stored [B][C][G] (V: [B][G]); per-instance
+    // point parameters (beta) and magnetisations on the device, or null when B = 1
+    int B;
+    const void* ppb;          // PointParams[B]
+    const double* Mb;         // M[B]
 };
 
 // Kernel identities for the per-kernel launch counter and event timer.
@@ -99,8 +111,8 @@ template <typename T> struct Ops {
                     int slot, cudaStream_t s);
     static int bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
                       int slot, cudaStream_t s);
-    static int ratio(const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
-                     cudaStream_t s);
+    static int ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp,
+                     double eps, cudaStream_t s);
     static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
     static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
                     cudaStream_t s);

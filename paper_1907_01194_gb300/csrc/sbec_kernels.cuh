@@ -65,6 +65,8 @@ struct XArgs {
     double* partials;
     int nblk;
     PointParams pp;
+    long long rpi;              // grid rows (x lines) per instance
+    const PointParams* ppb;     // per-instance point parameters (batches) or null
 };
 
 template <typename T, int F, int MODE, int ITEMS>
@@ -76,11 +78,17 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     T2* buf = reinterpret_cast<T2*>(smem_raw);
     const int logn = a.logn, n = 1 << logn;
     const int RPB = a.rpb, P = RPB * C;
-    const long long row0 = (long long)blockIdx.x * RPB;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in);
+    // instance of this block (blocks never straddle instances) and its offsets
+    const long long growrow = (long long)blockIdx.x * RPB;
+    const long long inst = growrow / a.rpi;
+    const long long row0 = growrow - inst * a.rpi;
+    const long long foff = inst * (long long)C * a.G;
+    const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + foff;
     const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
-    const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V);
+    const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * a.G;
+    const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
+    const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
 
     for (int idx = tid; idx < P * n; idx += nth) {
         const int p = idx >> logn, e = idx & (n - 1);
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             for (int c = 0; c < C; ++c) x[c] = buf[(rg * C + c) * n + e];
             Dens<F, T2> D;
             D.compute(x);
-            acc[0] += D.energy_density(x, double(Vp[(row0 + rg) * n + e]), a.pp);
+            acc[0] += D.energy_density(x, double(Vp[(row0 + rg) * n + e]), pp);
         }
         __syncthreads();
     }
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     if (inv) fft_pencils<T2, true, ITEMS>(buf, logn, P, n, 1, tw, tid, nth);
 
     if (MODE == X_FWD || MODE == X_FWD_EPW || MODE == X_INV) {
-        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out) + foff;
         for (int idx = tid; idx < P * n; idx += nth) {
             const int p = idx >> logn, e = idx & (n - 1);
             const int rg = p / C, c = p - rg * C;
@@ -138,8 +146,8 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     }
 
     if (MODE == X_INV_GRAD || MODE == X_FULL_GRAD) {
-        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X);
-        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X) + foff;
+        T2* __restrict__ dst = a.out ? reinterpret_cast<T2*>(a.out) + foff : nullptr;
         for (int idx = tid; idx < RPB * n; idx += nth) {
             const int rg = idx >> logn, e = idx & (n - 1);
             const long long pt = (row0 + rg) * n + e;
@@ -152,11 +160,11 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             const T V = Vp[pt];
             Dens<F, T2> D;
             D.compute(x);
-            grad_point<F, T2>(x, D, V, a.pp, lx, g);
+            grad_point<F, T2>(x, D, V, pp, lx, g);
             double ek = 0.0;
 #pragma unroll
             for (int c = 0; c < C; ++c) ek += double(x[c].x * lx[c].x + x[c].y * lx[c].y);
-            acc[0] += 0.5 * ek + D.energy_density(x, double(V), a.pp);
+            acc[0] += 0.5 * ek + D.energy_density(x, double(V), pp);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 acc[1 + c] += double(cabs2(x[c]));
@@ -167,9 +175,9 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     }
 
     if (MODE == X_INV_HESS || MODE == X_FULL_HESS) {
-        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X);
-        const T2* __restrict__ Zp = reinterpret_cast<const T2*>(a.Zd);
-        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
+        const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X) + foff;
+        const T2* __restrict__ Zp = reinterpret_cast<const T2*>(a.Zd) + foff;
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out) + foff;
         for (int idx = tid; idx < RPB * n; idx += nth) {
             const int rg = idx >> logn, e = idx & (n - 1);
             const long long pt = (row0 + rg) * n + e;
@@ -183,11 +191,11 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             const T V = Vp[pt];
             Dens<F, T2> D;
             D.compute(x);
-            hess_point<F, T2>(x, z, D, V, a.pp, lz, h);
+            hess_point<F, T2>(x, z, D, V, pp, lz, h);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 T s = T(a.sigma);
-                if (a.riem) s -= T(a.scal[SBEC_S_ALPHA_G] + a.scal[SBEC_S_BETA_G] * double(F - c));
+                if (a.riem) s -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
                 caxpy(h[c], s, z[c]);
                 acc[c] += double(cabs2(x[c]));
                 acc[C + c] += double(x[c].x * h[c].x + x[c].y * h[c].y);
@@ -273,14 +281,17 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
 // Elementwise kernels over grid points (grid-stride), all C components per point.
 // ---------------------------------------------------------------------------
 
+// Elementwise kernels: blockIdx.y is the instance of a batch, blockIdx.x strides
+// over its G grid points; partials of instance b are blocks b*gridDim.x ...
+
 // partials: n_l = |u_l|^2 (q = l index), t_l = <u_l, w_l> (q = C + l)
 template <typename T, int F>
-__global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials,
-                                                    int nblk) {
+__global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
-    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp);
+    const long long foff = (long long)blockIdx.y * C * G;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
+    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
     double acc[2 * C];
 #pragma unroll
     for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0;
@@ -292,19 +303,21 @@ __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* 
             acc[C + c] += double(u.x * w.x + u.y * w.y);
         }
     }
-    block_reduce_store<2 * C>(acc, partials, nblk, blockIdx.x);
+    block_reduce_store<2 * C>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // out_l = W_l - (alpha + beta l) U_l with (alpha, beta) = scal[ia], scal[ib]; partial |out|^2
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* Wp, void* Op, long long G,
-                                                    const double* __restrict__ scal, int ia, int ib,
-                                                    double* partials, int nblk) {
+                                                    const double* __restrict__ scal0, int ia, int ib,
+                                                    double* partials) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
-    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp);
-    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    const long long foff = (long long)blockIdx.y * C * G;
+    const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
+    const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
+    T2* __restrict__ O = Op ? reinterpret_cast<T2*>(Op) + foff : nullptr;
     T coef[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) coef[c] = T(scal[ia] + scal[ib] * double(F - c));
@@ -319,18 +332,19 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
             if (O) O[c * G + p] = w;
         }
     }
-    block_reduce_store<1>(acc, partials, nblk, blockIdx.x);
+    block_reduce_store<1>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // w = U + t Xi into out; partials m_l = |w_l|^2
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
-                                                   double* partials, int nblk) {
+                                                   double* partials) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up);
-    const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp);
-    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    const long long foff = (long long)blockIdx.y * C * G;
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
+    const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
     double acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = 0.0;
@@ -344,15 +358,17 @@ __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* X
             O[c * G + p] = w;
         }
     }
-    block_reduce_store<C>(acc, partials, nblk, blockIdx.x);
+    block_reduce_store<C>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // out_l *= scal[S_SIG + l]
 template <typename T, int F>
-__global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal) {
+__global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal0) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    T2* __restrict__ O = reinterpret_cast<T2*>(Op);
+    const long long foff = (long long)blockIdx.y * C * G;
+    const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
     T s[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) s[c] = T(scal[S_SIG + c]);
@@ -372,14 +388,15 @@ static __device__ __forceinline__ void set_status(double* scal, int code) {
 
 // Warp-parallel fixed-order sums: warp w of the block reduces quantities
 // q = w, w + nwarps, ...; lane-strided loads then a shuffle tree, so each sum
-// has a fixed order for a given nblk.  vals[q] is valid after the barrier.
-__device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int na, const int* qs, int nq,
-                                          double* vals) {
+// has a fixed order.  Quantity q of instance b is partials[q * ntot + off ..
+// off + cnt - 1] with off = b * cnt.  vals[k] is valid after the barrier.
+__device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int ntot, int off, int cnt, const int* qs,
+                                          int nq, double* vals) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = warp; k < nq; k += nw) {
-        const double* src = pa + (size_t)qs[k] * na;
+        const double* src = pa + (size_t)qs[k] * ntot + off;
         double s = 0.0;
-        for (int i = lane; i < na; i += 32) s += src[i];
+        for (int i = lane; i < cnt; i += 32) s += src[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) vals[k] = s;
@@ -387,13 +404,19 @@ __device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int na,
     __syncthreads();
 }
 
+// Finalize kernels: one block per instance (blockIdx.x), whose partials are the
+// per-instance slices of na_inst blocks inside the na_tot blocks of the launch.
+
 // energy: scal[E] = sum of partA quantities 0..nqa-1 (+ partB quantity 0)
-static __global__ void k_fin_energy(const double* pa, int na, int nqa, const double* pb, int nb, double* scal) {
+static __global__ void k_fin_energy(const double* pa, int na_tot, int na_inst, int nqa, const double* pb, int nb_tot,
+                                    int nb_inst, double* scal0) {
     __shared__ double va[4], vb[1];
+    const int b = blockIdx.x;
     const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
-    warp_sums(pa, na, qa, nqa, va);
-    if (pb) warp_sums(pb, nb, qb, 1, vb);
+    warp_sums(pa, na_tot, b * na_inst, na_inst, qa, nqa, va);
+    if (pb) warp_sums(pb, nb_tot, b * nb_inst, nb_inst, qb, 1, vb);
     if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)b * S_COUNT;
         double e = 0.0;
         for (int q = 0; q < nqa; ++q) e += va[q];
         if (pb) e += vb[0];
@@ -405,21 +428,24 @@ static __global__ void k_fin_energy(const double* pa, int na, int nqa, const dou
 // gradient / projection coefficients (Lemma 4.1, Eq. ab) from n_l (q = qn + l) and
 // t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
 // beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
-static __global__ void k_fin_proj(const double* pa, int na, int F, int qe, int qn, int qt, double M, double* scal,
-                                  int slot_a, int slot_b, int write_grad_info) {
+static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int F, int qe, int qn, int qt, double M0,
+                                  const double* Mb, double* scal0, int slot_a, int slot_b, int write_grad_info) {
     const int C = 2 * F + 1;
+    const int b = blockIdx.x;
     __shared__ double v[15];
     int qs[15];
     int nq = 0;
     for (int i = 0; i < C; ++i) qs[nq++] = qn + i;
     for (int i = 0; i < C; ++i) qs[nq++] = qt + i;
     if (qe >= 0) qs[nq++] = qe;
-    warp_sums(pa, na, qs, nq, v);
+    warp_sums(pa, na_tot, b * na_inst, na_inst, qs, nq, v);
     if (threadIdx.x == 0) {
-        double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, b = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
+        double* scal = scal0 + (size_t)b * S_COUNT;
+        const double M = Mb ? Mb[b] : M0;
+        double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, bb = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
         for (int i = 0; i < C; ++i) {
             const double l = double(F - i), nl = v[i], tl = v[C + i];
-            a += nl; b += l * nl; c += l * l * nl;
+            a += nl; bb += l * nl; c += l * l * nl;
             ug += tl; uGg += l * tl;
         }
         const double au = c - M * M;
@@ -432,18 +458,19 @@ static __global__ void k_fin_proj(const double* pa, int na, int F, int qe, int q
         if (write_grad_info) {
             scal[SBEC_S_ENERGY] = e;
             scal[SBEC_S_MASS] = a;
-            scal[SBEC_S_MAG] = b;
+            scal[SBEC_S_MAG] = bb;
             scal[S_C2] = c;
             if (!isfinite(e) || !isfinite(al) || !isfinite(be)) set_status(scal, SBEC_ERR_NONFINITE);
         }
     }
 }
 
-static __global__ void k_fin_norm(const double* pa, int na, double* scal, int slot) {
+static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, double* scal0, int slot) {
     __shared__ double v[1];
     const int q[1] = {0};
-    warp_sums(pa, na, q, 1, v);
+    warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, q, 1, v);
     if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
         scal[slot] = v[0];
         if (!isfinite(v[0])) set_status(scal, SBEC_ERR_NONFINITE);
     }
@@ -458,12 +485,15 @@ static __global__ void k_fin_norm(const double* pa, int na, double* scal, int sl
 //    safeguarded Newton.
 //  kind 3, Lemma 5.4: closed form.
 // Both iterations stop when the step is below 4 ulps of r or after 200 steps.
-static __global__ void k_retract_solve(const double* pa, int na, int F, double M, int kind, double* scal) {
+static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst, int F, double M0, const double* Mb,
+                                       int kind, double* scal0) {
     __shared__ double m[7];
     const int C = 2 * F + 1;
     const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
-    warp_sums(pa, na, qs, C, m);
+    warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, C, m);
     if (threadIdx.x != 0) return;
+    double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
+    const double M = Mb ? Mb[blockIdx.x] : M0;
     double sig[7];
     for (int i = 0; i < 7; ++i) sig[i] = 0.0;
     // f2 = largest l with w_l != 0 (component index i1), f1 = smallest (index i2)
@@ -573,14 +603,17 @@ static __global__ void k_retract_solve(const double* pa, int na, int F, double M
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const double* __restrict__ scal,
-                                                 double* partials, int nblk) {
-    // out may alias A, B, D1 or D2 (same index only), so no __restrict__ here
-    const T* A = reinterpret_cast<const T*>(L.A);
-    const T* B = reinterpret_cast<const T*>(L.B);
-    const T* D1 = reinterpret_cast<const T*>(L.D1);
-    const T* D2 = reinterpret_cast<const T*>(L.D2);
-    T* O = reinterpret_cast<T*>(L.out);
+__global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const double* __restrict__ scal0,
+                                                 double* partials) {
+    // out may alias A, B, D1 or D2 (same index only), so no __restrict__ here;
+    // blockIdx.y is the instance, N the reals per instance
+    const long long off = (long long)blockIdx.y * N;
+    const double* scal = scal0 + (size_t)blockIdx.y * S_COUNT;
+    const T* A = reinterpret_cast<const T*>(L.A) + off;
+    const T* B = L.B ? reinterpret_cast<const T*>(L.B) + off : nullptr;
+    const T* D1 = L.D1 ? reinterpret_cast<const T*>(L.D1) + off : nullptr;
+    const T* D2 = L.D2 ? reinterpret_cast<const T*>(L.D2) + off : nullptr;
+    T* O = reinterpret_cast<T*>(L.out) + off;
     const bool self1 = (L.D1 == L.out), self2 = (L.D2 == L.out);
     double ca = L.ca, cb = L.cb;
     if (L.ia >= 0) ca *= scal[L.ia];
@@ -600,33 +633,35 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
         if (D1) acc[0] += double(v) * (self1 ? double(v) : double(D1[i]));
         if (D2) acc[1] += double(v) * (self2 ? double(v) : double(D2[i]));
     }
-    if (partials) block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+    if (partials) block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // partials q0 = <A, B>, q1 = <C, D> (C null: skip)
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, const void* Cp, const void* Dp,
-                                              long long N, double* partials, int nblk) {
-    const T* __restrict__ A = reinterpret_cast<const T*>(Ap);
-    const T* __restrict__ B = reinterpret_cast<const T*>(Bp);
-    const T* __restrict__ Cv = reinterpret_cast<const T*>(Cp);
-    const T* __restrict__ D = reinterpret_cast<const T*>(Dp);
+                                              long long N, double* partials) {
+    const long long off = (long long)blockIdx.y * N;
+    const T* __restrict__ A = reinterpret_cast<const T*>(Ap) + off;
+    const T* __restrict__ B = reinterpret_cast<const T*>(Bp) + off;
+    const T* __restrict__ Cv = Cp ? reinterpret_cast<const T*>(Cp) + off : nullptr;
+    const T* __restrict__ D = Dp ? reinterpret_cast<const T*>(Dp) + off : nullptr;
     double acc[2] = {0.0, 0.0};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         acc[0] += double(A[i]) * double(B[i]);
         if (Cv) acc[1] += double(Cv[i]) * double(D[i]);
     }
-    block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+    block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // partials q0 = <u - up, g - gp>, q1 = |g - gp|^2 (the BB quantities s^T v, v^T v)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp, const void* Gp, const void* GPp,
-                                                long long N, double* partials, int nblk) {
-    const T* __restrict__ U = reinterpret_cast<const T*>(Up);
-    const T* __restrict__ UP = reinterpret_cast<const T*>(UPp);
-    const T* __restrict__ G = reinterpret_cast<const T*>(Gp);
-    const T* __restrict__ GP = reinterpret_cast<const T*>(GPp);
+                                                long long N, double* partials) {
+    const long long off = (long long)blockIdx.y * N;
+    const T* __restrict__ U = reinterpret_cast<const T*>(Up) + off;
+    const T* __restrict__ UP = reinterpret_cast<const T*>(UPp) + off;
+    const T* __restrict__ G = reinterpret_cast<const T*>(Gp) + off;
+    const T* __restrict__ GP = reinterpret_cast<const T*>(GPp) + off;
     double acc[2] = {0.0, 0.0};
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const double sv = double(U[i]) - double(UP[i]);
@@ -634,15 +669,16 @@ __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp,
         acc[0] += sv * vv;
         acc[1] += vv * vv;
     }
-    block_reduce_store<2>(acc, partials, nblk, blockIdx.x);
+    block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-// scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2)
-static __global__ void k_fin_sums(const double* pa, int na, int nq, double* scal, int slot) {
+// scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2), per instance
+static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int nq, double* scal0, int slot) {
     __shared__ double v[2];
     const int qs[2] = {0, 1};
-    warp_sums(pa, na, qs, nq, v);
+    warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, nq, v);
     if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
         for (int q = 0; q < nq; ++q) {
             scal[slot + q] = v[q];
             if (!isfinite(v[q])) set_status(scal, SBEC_ERR_NONFINITE);
@@ -650,13 +686,15 @@ static __global__ void k_fin_sums(const double* pa, int na, int nq, double* scal
     }
 }
 
-// scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha, beta)
-static __global__ void k_ratio(double* scal, int dst, int num, int den, int guard_kap, int guard_pp, double eps) {
+// scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha), per
+// instance; scal[dst + 1] is the guard flag of the guarded updates
+static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps) {
     if (threadIdx.x != 0) return;
+    double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
     bool ok = true;
     if (guard_kap >= 0) ok = scal[guard_kap] > eps * scal[guard_pp];
     scal[dst] = ok ? scal[num] / scal[den] : 0.0;
-    scal[dst + 1] = ok ? 1.0 : 0.0;       // guard flag for the guarded updates
+    scal[dst + 1] = ok ? 1.0 : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -734,16 +772,17 @@ __global__ void k_convert(void* Vp, const double* Vd, long long G) {
 // ---------------------------------------------------------------------------
 // Launch configuration
 // ---------------------------------------------------------------------------
-struct XCfg { int rpb, nth, items, nblk; size_t smem; };
-struct SCfg { int W, nth, items, nblk; size_t smem; };
+struct XCfg { int rpb, nth, items, nblk, nblk_inst; size_t smem; };
+struct SCfg { int W, nth, items, nblk, nblk_inst; size_t smem; };
 
+// x pass: one block = rpb grid rows (x lines) of all C components of one instance
 template <typename T>
 static XCfg xcfg(const Geom& g) {
     using T2 = typename C2<T>::t;
     const int n = g.n[0];
-    const long long rows = g.G / n;
+    const long long rows_inst = g.G / n;
     int rpb = 1;
-    while ((long long)rpb * 2 * g.C * n <= 2048 && rows % (rpb * 2) == 0) rpb *= 2;
+    while ((long long)rpb * 2 * g.C * n <= 2048 && rows_inst % (rpb * 2) == 0) rpb *= 2;
     const int P = rpb * g.C;
     const int bfly = (n >= 4) ? P * n / 4 : P;
     int nth = ((bfly + 31) / 32) * 32;
@@ -753,11 +792,14 @@ static XCfg xcfg(const Geom& g) {
     int it2 = 1;
     while (it2 < items) it2 *= 2;
     XCfg c;
-    c.rpb = rpb; c.nth = nth; c.items = it2; c.nblk = (int)(rows / rpb);
+    c.rpb = rpb; c.nth = nth; c.items = it2;
+    c.nblk_inst = (int)(rows_inst / rpb);
+    c.nblk = c.nblk_inst * g.B;
     c.smem = (size_t)P * n * sizeof(T2);
     return c;
 }
 
+// strided pass: one block = W consecutive x columns of one component of one instance
 template <typename T>
 static SCfg scfg(const Geom& g, int axis, int num_sms) {
     using T2 = typename C2<T>::t;
@@ -767,7 +809,7 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
     int W = (sizeof(T) == 8) ? 8 : 16;
     if (W > nx) W = nx;
     // prefer at least 4 blocks per SM when the grid is small
-    while (W > 2 && (long long)g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
+    while (W > 2 && (long long)g.B * g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
     const int bfly = (n >= 4) ? W * n / 4 : W;
     int nth = ((bfly + 31) / 32) * 32;
     if (nth > 512) nth = 512;
@@ -777,14 +819,17 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
     while (it2 < items) it2 *= 2;
     SCfg c;
     c.W = W; c.nth = nth; c.items = it2;
-    c.nblk = (int)((long long)g.C * outer * (nx / W));
+    c.nblk_inst = (int)((long long)g.C * outer * (nx / W));
+    c.nblk = c.nblk_inst * g.B;
     c.smem = (size_t)W * n * sizeof(T2);
     return c;
 }
 
-static int elem_blocks(long long G, int num_sms) {
+// blocks per instance of the grid-stride elementwise kernels
+static int elem_blocks(long long G, int num_sms, int B = 1) {
     long long b = (G + 255) / 256;
-    const long long cap = 8LL * num_sms;
+    long long cap = 8LL * num_sms / (B > 0 ? B : 1);
+    if (cap < 1) cap = 1;
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -893,6 +938,8 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.sigma = 0.0; a.scal = nullptr; a.riem = 0;
     a.partials = part; a.nblk = c.nblk;
     a.pp = point_params(g);
+    a.rpi = g.G / g.n[0];
+    a.ppb = reinterpret_cast<const PointParams*>(g.ppb);
     return a;
 }
 
@@ -938,11 +985,13 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         st = launch_x<T, F, X_INV_GRAD>(c, a, w, s);
         if (st) return st;
     }
-    SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partA, c.nblk, F, 0, 1, 1 + C, g.M, w.scal, SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+    SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
     if (Griem || want_norm) {
-        const int nb = elem_blocks(g.G, w.num_sms);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G, SBEC_S_BETA_G, w.partB, nb);
-        SBEC_LAUNCH(K_FIN, k_fin_norm, 1, 256, w.partB, nb, w.scal, SBEC_S_RGRAD_NORM2);
+        const int nb = elem_blocks(g.G, w.num_sms, g.B);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
+                    SBEC_S_BETA_G, w.partB);
+        SBEC_LAUNCH(K_FIN, k_fin_norm, g.B, 256, w.partB, nb * g.B, nb, w.scal, SBEC_S_RGRAD_NORM2);
     }
     return SBEC_OK;
 }
@@ -954,25 +1003,25 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
     if (g.dim == 1) {
         st = launch_x<T, F, X_FULL_ENERGY>(c, xargs<T>(g, c, X, nullptr, w.partA), w, s);
         if (st) return st;
-        SBEC_LAUNCH(K_FIN, k_fin_energy, 1, 256, w.partA, c.nblk, 2, nullptr, 0, w.scal);
+        SBEC_LAUNCH(K_FIN, k_fin_energy, g.B, 256, w.partA, c.nblk, c.nblk_inst, 2, nullptr, 0, 0, w.scal);
         return SBEC_OK;
     }
     st = launch_x<T, F, X_FWD_EPW>(c, xargs<T>(g, c, X, w.work, w.partA), w, s);
     if (st) return st;
-    int nbB;
+    SCfg cl;
     if (g.dim == 2) {
-        const SCfg cy = scfg<T>(g, 1, w.num_sms);
-        st = launch_s<T, S_PARSEVAL>(cy, sargs<T>(g, cy, 1, w.work, nullptr, w.partB), w, s);
-        nbB = cy.nblk;
+        cl = scfg<T>(g, 1, w.num_sms);
+        st = launch_s<T, S_PARSEVAL>(cl, sargs<T>(g, cl, 1, w.work, nullptr, w.partB), w, s);
     } else {
-        const SCfg cy = scfg<T>(g, 1, w.num_sms), cz = scfg<T>(g, 2, w.num_sms);
+        const SCfg cy = scfg<T>(g, 1, w.num_sms);
+        cl = scfg<T>(g, 2, w.num_sms);
         st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
         if (st) return st;
-        st = launch_s<T, S_PARSEVAL>(cz, sargs<T>(g, cz, 2, w.work, nullptr, w.partB), w, s);
-        nbB = cz.nblk;
+        st = launch_s<T, S_PARSEVAL>(cl, sargs<T>(g, cl, 2, w.work, nullptr, w.partB), w, s);
     }
     if (st) return st;
-    SBEC_LAUNCH(K_FIN, k_fin_energy, 1, 256, w.partA, c.nblk, 1, w.partB, nbB, w.scal);
+    SBEC_LAUNCH(K_FIN, k_fin_energy, g.B, 256, w.partA, c.nblk, c.nblk_inst, 1, w.partB, cl.nblk, cl.nblk_inst,
+                w.scal);
     return SBEC_OK;
 }
 
@@ -980,13 +1029,15 @@ template <typename T, int F>
 static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
                   cudaStream_t s) {
     constexpr int C = 2 * F + 1;
-    const int nb = elem_blocks(g.G, w.num_sms);
+    const int nb = elem_blocks(g.G, w.num_sms, g.B);
     const void* zin = Z;
     if (riem) {
         // xi = P_u Z (Lemma 4.1)
-        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), nb, 256, X, Z, g.G, w.partB, nb);
-        SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partB, nb, F, -1, 0, C, g.M, w.scal, S_PA, S_PB, 0);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB, w.partB, nb);
+        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.B), 256, X, Z, g.G, w.partB);
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partB, nb * g.B, nb, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA, S_PB,
+                    0);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB,
+                    w.partB);
         zin = w.work2;
     }
     const XCfg c = xcfg<T>(g);
@@ -1009,8 +1060,9 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (st) return st;
     }
     if (riem) {
-        SBEC_LAUNCH(K_FIN, k_fin_proj, 1, 256, w.partA, c.nblk, F, -1, 0, C, g.M, w.scal, S_PA, S_PB, 0);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), nb, 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB, nb);
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, c.nblk, c.nblk_inst, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA,
+                    S_PB, 0);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB);
     }
     return SBEC_OK;
 }
@@ -1018,10 +1070,10 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
 template <typename T, int F>
 static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
                      cudaStream_t s) {
-    const int nb = elem_blocks(g.G, w.num_sms);
-    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), nb, 256, U, Xi, t, out, g.G, w.partB, nb);
-    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, 1, 256, w.partB, nb, F, g.M, kind, w.scal);
-    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), nb, 256, out, g.G, w.scal);
+    const int nb = elem_blocks(g.G, w.num_sms, g.B);
+    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.B), 256, U, Xi, t, out, g.G, w.partB);
+    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.B, 256, w.partB, nb * g.B, nb, F, g.M, g.Mb, kind, w.scal);
+    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.B), 256, out, g.G, w.scal);
     return SBEC_OK;
 }
 
@@ -1067,10 +1119,10 @@ int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi,
 template <typename T>
 int Ops<T>::lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
     const bool dots = (L.D1 || L.D2);
-    SBEC_LAUNCH(K_LIN, k_lincomb<T>, nb, 256, L, N, w.scal, dots ? w.partB : nullptr, nb);
-    if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, 2, w.scal, dot_slot);
+    SBEC_LAUNCH(K_LIN, k_lincomb<T>, dim3(nb, g.B), 256, L, N, w.scal, dots ? w.partB : nullptr);
+    if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, dot_slot);
     return SBEC_OK;
 }
 
@@ -1078,9 +1130,9 @@ template <typename T>
 int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, const void* C, const void* D, int slot,
                  cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms);
-    SBEC_LAUNCH(K_DOT, k_dot2<T>, nb, 256, A, B, C, D, N, w.partB, nb);
-    SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, C ? 2 : 1, w.scal, slot);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
+    SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.B), 256, A, B, C, D, N, w.partB);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, C ? 2 : 1, w.scal, slot);
     return SBEC_OK;
 }
 
@@ -1088,21 +1140,23 @@ template <typename T>
 int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
                    int slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms);
-    SBEC_LAUNCH(K_DOT, k_bbdots<T>, nb, 256, U, UP, Gv, GP, N, w.partB, nb);
-    SBEC_LAUNCH(K_FIN, k_fin_sums, 1, 256, w.partB, nb, 2, w.scal, slot);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
+    SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.B), 256, U, UP, Gv, GP, N, w.partB);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, slot);
     return SBEC_OK;
 }
 
 template <typename T>
-int Ops<T>::ratio(const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps, cudaStream_t s) {
-    SBEC_LAUNCH(K_FIN, k_ratio, 1, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps);
+int Ops<T>::ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
+                  cudaStream_t s) {
+    SBEC_LAUNCH(K_FIN, k_ratio, g.B, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps);
     return SBEC_OK;
 }
 
 template <typename T, int F>
 static int prolongate_F(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf, void* Xf,
                         cudaStream_t s) {
+    if (gc.B != 1 || gf.B != 1) return SBEC_ERR_ARG;
     // coarse forward transform into the coarse scratch
     {
         const Work& w = wc;
@@ -1176,7 +1230,7 @@ template <typename T>
 size_t Ops<T>::partials_needed(const Geom& g, int num_sms) {
     const XCfg c = xcfg<T>(g);
     size_t need = (size_t)c.nblk * (1 + 2 * g.C);
-    const size_t e = (size_t)elem_blocks(g.G, num_sms) * (2 * g.C);
+    const size_t e = (size_t)elem_blocks(g.G, num_sms, g.B) * g.B * (2 * g.C);
     if (e > need) need = e;
     for (int ax = 1; ax < g.dim; ++ax) {
         const SCfg sc = scfg<T>(g, ax, num_sms);

@@ -170,7 +170,7 @@ struct Solver {
                     const int rr_now = (j & 1) ? SL_RRB : SL_RRA, rr_next = (j & 1) ? SL_RRA : SL_RRB;
                     TRY(hess(u, p, sigma, 1, Hp));
                     TRY(Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, s));
-                    TRY(Ops<T>::ratio(w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s));
+                    TRY(Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s));
                     TRY(lin(x, 1.0, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1));
                     TRY(lin(r, 1.0, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, nullptr, rr_next));
                     PULL(ds);
@@ -301,6 +301,7 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
                sbec_stats* stats) {
     if (!h || !X || !workspace) return SBEC_ERR_ARG;
     if (workspace_bytes < 10 * h->field_bytes || !sbec_is_device_ptr(workspace)) return SBEC_ERR_ARG;
+    if (h->B != 1) return SBEC_ERR_ARG;       // batches: sbec_solve_batch
     sbec_solve_opts o;
     if (opts) o = *opts; else sbec_solve_defaults(&o);
     if (o.retraction < 1 || o.retraction > 3 || !(o.tol > 0.0) || o.maxit < 0 || o.rgbb_maxit < 0) return SBEC_ERR_ARG;

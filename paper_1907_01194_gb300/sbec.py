@@ -48,6 +48,10 @@ _lib.sbec_retract.argtypes = [_vp, _vp, _vp, _dbl, _int, _vp]
 _lib.sbec_sync.argtypes = [_vp]
 _lib.sbec_scalars.argtypes = [_vp]
 _lib.sbec_scalars.restype = _vp
+_lib.sbec_create_batch.argtypes = [ctypes.POINTER(Problem), _int, _vp, _vp, ctypes.POINTER(_vp)]
+_lib.sbec_create_batch.restype = _int
+_lib.sbec_batch_size.argtypes = [_vp]
+_lib.sbec_batch_size.restype = _int
 _lib.sbec_launch_count.argtypes = [_vp]
 _lib.sbec_launch_count.restype = ctypes.c_longlong
 _lib.sbec_profile.argtypes = [_vp, _int]
@@ -122,6 +126,48 @@ class Handle:
         _check(_lib.sbec_create(ctypes.byref(pr), _ptr(V) if V is not None else None, stream,
                                 ctypes.byref(out)), "sbec_create")
         self._h = out
+        self.B = 1
+
+    @classmethod
+    def batch(cls, workloads, precision="fp64", V="auto", stream=None):
+        """One batch handle (sbec_create_batch) for workloads that share spin, grid, box and
+        Zeeman terms; arrays are then (B, C, ...) and scalar outputs have B entries."""
+        from . import workloads as W
+        ws = list(workloads)
+        B = len(ws)
+        probs = (Problem * B)()
+        for i, w in enumerate(ws):
+            n = tuple(int(v) for v in w.n)
+            dim = len(n)
+            pr = probs[i]
+            pr.F, pr.dim = int(w.F), dim
+            for a in range(3):
+                pr.n[a] = n[a] if a < dim else 1
+                pr.lo[a] = float(w.lo[a]) if a < dim else 0.0
+                pr.hi[a] = float(w.hi[a]) if a < dim else 1.0
+            b = tuple(w.beta) + (0.0,) * (4 - len(w.beta))
+            for a in range(4):
+                pr.beta[a] = float(b[a])
+            pr.p, pr.q, pr.M = float(w.p), float(w.q), float(w.M)
+            pr.precision = FP64 if precision == "fp64" else MIXED
+        if isinstance(V, str) and V == "auto":
+            V = np.ascontiguousarray(np.stack([W.potential(w) for w in ws]), dtype=np.float64)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self = cls.__new__(cls)
+        self.problem = probs[0]
+        self.F, self.C, self.n, self.dim = int(ws[0].F), ws[0].C, tuple(ws[0].n), len(ws[0].n)
+        self.precision = precision
+        self.shape = (B, self.C) + tuple(reversed(self.n))
+        self.stream = stream
+        self._V_keep = V
+        out = _vp()
+        _check(_lib.sbec_create_batch(probs, B, _ptr(V) if V is not None else None, stream, ctypes.byref(out)),
+               "sbec_create_batch")
+        self._h = out
+        self.B = B
+        return self
 
     @classmethod
     def from_workload(cls, w, precision="fp64", V="auto", stream=None):
@@ -149,18 +195,22 @@ class Handle:
         self.close()
 
     # -- calls -------------------------------------------------------------
+    def _out(self, arr):
+        return arr[0] if self.B == 1 else np.array(arr[:])
+
     def energy(self, X, sync=True):
-        E = ctypes.c_double()
-        _check(_lib.sbec_energy(self._h, _ptr(X), ctypes.byref(E) if sync else None), "sbec_energy")
-        return E.value if sync else None
+        """E_h(X); an array of B values for a batch handle."""
+        E = (ctypes.c_double * self.B)()
+        _check(_lib.sbec_energy(self._h, _ptr(X), E if sync else None), "sbec_energy")
+        return self._out(E) if sync else None
 
     def grad(self, X, G_euc=None, G_riem=None, sync=True):
-        """Returns (E, ||grad E||_2) when sync, else None (values stay on the device)."""
-        E, rn = ctypes.c_double(), ctypes.c_double()
+        """Returns (E, ||grad E||_2) when sync (arrays of B values for a batch handle),
+        else None (values stay on the device)."""
+        E, rn = (ctypes.c_double * self.B)(), (ctypes.c_double * self.B)()
         _check(_lib.sbec_grad(self._h, _ptr(X), _ptr(G_euc), _ptr(G_riem),
-                              ctypes.byref(E) if sync else None,
-                              ctypes.byref(rn) if sync else None), "sbec_grad")
-        return (E.value, rn.value) if sync else None
+                              E if sync else None, rn if sync else None), "sbec_grad")
+        return (self._out(E), self._out(rn)) if sync else None
 
     def hessvec(self, X, Z, HZ, sigma=0.0, riemannian=False):
         _check(_lib.sbec_hessvec(self._h, _ptr(X), _ptr(Z), float(sigma), int(bool(riemannian)),
