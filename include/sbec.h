@@ -158,6 +158,14 @@ int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes);
 int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
                sbec_stats* stats);
 
+/* sbec_solve for a batch handle: all instances iterate in lock step (one launch
+ * per pass covers the batch); each instance takes the decisions sbec_solve
+ * would take for it alone and stops when it converges.  X: device array of the
+ * batch; stats: B entries.  Returns SBEC_ERR_NOCONV if any instance did not
+ * reach the tolerance. */
+int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                     sbec_stats* stats);
+
 /* Mixed-precision solve with FP64 refinement: X (complex128, device) is cast to
  * float, solved on h32 (precision SBEC_MIXED, same problem and stream as h64)
  * to max(tol_mixed, opts->tol), cast back, projected on M and refined on h64

@@ -112,14 +112,15 @@ template <typename T> struct Ops {
     static int bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
                       int slot, cudaStream_t s);
     static int ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp,
-                     double eps, cudaStream_t s);
+                     double eps, cudaStream_t s, int mask = -1);
     static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
     static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
                     cudaStream_t s);
+    // sigslot / tslot >= 0: sigma / t multiplied by each instance's scalar-block slot
     static int hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem,
-                       void* HZ, cudaStream_t s);
+                       void* HZ, cudaStream_t s, int sigslot = -1);
     static int retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind,
-                       void* out, cudaStream_t s);
+                       void* out, cudaStream_t s, int tslot = -1);
     static int prolongate(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf,
                           void* Xf, cudaStream_t s);
     static int init_tables(Geom& g, void* tw_storage, cudaStream_t s);

@@ -62,6 +62,7 @@ struct XArgs {
     double sigma;         // Hessian shift
     const double* scal;   // device scalar block: Lemma 4.2 alpha_g, beta_g (riemannian epilogue)
     int riem;
+    int sigslot;          // >= 0: sigma is multiplied by the instance's scal[sigslot]
     double* partials;
     int nblk;
     PointParams pp;
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             hess_point<F, T2>(x, z, D, V, pp, lz, h);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                T s = T(a.sigma);
+                T s = T(a.sigslot >= 0 ? a.sigma * scal[a.sigslot] : a.sigma);
                 if (a.riem) s -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
                 caxpy(h[c], s, z[c]);
                 acc[c] += double(cabs2(x[c]));
@@ -338,10 +339,11 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
 // w = U + t Xi into out; partials m_l = |w_l|^2
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
-                                                   double* partials) {
+                                                   double* partials, const double* __restrict__ scal0, int tslot) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     const long long foff = (long long)blockIdx.y * C * G;
+    if (tslot >= 0) t *= scal0[(size_t)blockIdx.y * S_COUNT + tslot];
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
     T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
@@ -688,11 +690,12 @@ static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int
 
 // scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha), per
 // instance; scal[dst + 1] is the guard flag of the guarded updates
-static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps) {
+static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
+                               int mask) {
     if (threadIdx.x != 0) return;
     double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
-    bool ok = true;
-    if (guard_kap >= 0) ok = scal[guard_kap] > eps * scal[guard_pp];
+    bool ok = (mask < 0) || (scal[mask] != 0.0);
+    if (guard_kap >= 0) ok = ok && scal[guard_kap] > eps * scal[guard_pp];
     scal[dst] = ok ? scal[num] / scal[den] : 0.0;
     scal[dst + 1] = ok ? 1.0 : 0.0;
 }
@@ -935,7 +938,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     XArgs a;
     a.in = in; a.out = out; a.X = nullptr; a.Zd = nullptr; a.V = g.V; a.tw = g.tw[0];
     a.lam2x = g.lam2[0]; a.G = g.G; a.logn = g.logn[0]; a.rpb = c.rpb; a.invG = g.invG;
-    a.sigma = 0.0; a.scal = nullptr; a.riem = 0;
+    a.sigma = 0.0; a.scal = nullptr; a.riem = 0; a.sigslot = -1;
     a.partials = part; a.nblk = c.nblk;
     a.pp = point_params(g);
     a.rpi = g.G / g.n[0];
@@ -1027,7 +1030,7 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
 
 template <typename T, int F>
 static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
-                  cudaStream_t s) {
+                  cudaStream_t s, int sigslot = -1) {
     constexpr int C = 2 * F + 1;
     const int nb = elem_blocks(g.G, w.num_sms, g.B);
     const void* zin = Z;
@@ -1046,7 +1049,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
     int st;
     if (g.dim == 1) {
         XArgs a = xargs<T>(g, c, zin, HZ, w.partA);
-        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal;
+        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
         st = launch_x<T, F, X_FULL_HESS>(c, a, w, s);
         if (st) return st;
     } else {
@@ -1055,7 +1058,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         st = middle_passes<T>(g, w, s);
         if (st) return st;
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
-        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal;
+        a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
         st = launch_x<T, F, X_INV_HESS>(c, a, w, s);
         if (st) return st;
     }
@@ -1069,9 +1072,9 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
 
 template <typename T, int F>
 static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
-                     cudaStream_t s) {
+                     cudaStream_t s, int tslot = -1) {
     const int nb = elem_blocks(g.G, w.num_sms, g.B);
-    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.B), 256, U, Xi, t, out, g.G, w.partB);
+    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.B), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot);
     SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.B, 256, w.partB, nb * g.B, nb, F, g.M, g.Mb, kind, w.scal);
     SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.B), 256, out, g.G, w.scal);
     return SBEC_OK;
@@ -1102,16 +1105,16 @@ int Ops<T>::grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* 
 
 template <typename T>
 int Ops<T>::hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
-                    cudaStream_t s) {
-#define H_(F) hess_F<T, F>(g, w, X, Z, sigma, riem, HZ, s)
+                    cudaStream_t s, int sigslot) {
+#define H_(F) hess_F<T, F>(g, w, X, Z, sigma, riem, HZ, s, sigslot)
     SBEC_DISPATCH_F(H_)
 #undef H_
 }
 
 template <typename T>
 int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
-                    cudaStream_t s) {
-#define R_(F) retract_F<T, F>(g, w, U, Xi, t, kind, out, s)
+                    cudaStream_t s, int tslot) {
+#define R_(F) retract_F<T, F>(g, w, U, Xi, t, kind, out, s, tslot)
     SBEC_DISPATCH_F(R_)
 #undef R_
 }
@@ -1148,8 +1151,8 @@ int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, 
 
 template <typename T>
 int Ops<T>::ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
-                  cudaStream_t s) {
-    SBEC_LAUNCH(K_FIN, k_ratio, g.B, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps);
+                  cudaStream_t s, int mask) {
+    SBEC_LAUNCH(K_FIN, k_ratio, g.B, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps, mask);
     return SBEC_OK;
 }
 

@@ -25,6 +25,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "sbec_handle.h"
@@ -248,7 +250,8 @@ struct Solver {
         if (cudaMemcpyAsync(u, Xdev, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
         int ds;
         if (o.project_initial) {
-            TRY(retract(u, u, 0.0, u));
+            // P_M(X) (Lemma 5.1) whatever retraction the iteration uses
+            TRY(Ops<T>::retract(g, w, u, u, 0.0, 1, u, s));
             PULL(ds);
             if (ds) return ds;
         }
@@ -276,6 +279,357 @@ struct Solver {
 #undef PULL
 };
 
+// ---------------------------------------------------------------------------
+// Lock-step solver for a batch handle: every instance runs the same kernel
+// sequence; per-instance steps, sigma, CG coefficients and active / accept flags
+// live in each instance's scalar block and guard the updates, so finished
+// instances are left unchanged (or recomputed identically).  The decisions are
+// those of Solver<T> applied to each instance.
+// ---------------------------------------------------------------------------
+enum {
+    SL_T = SL_D0 + 14,      // step length per instance
+    SL_SIG = SL_D0 + 15,    // sigma per instance
+    SL_ACT = SL_D0 + 16,    // instance still iterating
+    SL_CG = SL_D0 + 17,     // instance still in the modified CG
+    SL_BETA = SL_D0 + 18,   // CG beta
+    SL_TAU = SL_D0 + 19,    // tau of Eq. (xi)
+    SL_NEG = SL_D0 + 20,    // xi = -grad
+    SL_HD = SL_D0 + 21,     // xi = s + tau d
+    SL_ACC = SL_D0 + 22,    // trial accepted
+};
+
+template <typename T>
+struct BatchSolver {
+    sbec_handle* h;
+    const sbec::Geom& g;
+    const sbec::Work& w;
+    cudaStream_t s;
+    sbec_solve_opts o;
+    sbec_stats* st;
+    int B;
+    void* f[10];
+    std::vector<int> dstat;
+
+    BatchSolver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt)
+        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), B(hh->B), dstat(hh->B, 0) {
+        char* b = static_cast<char*>(ws);
+        for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
+    }
+
+    double* hs(int b) { return h->h_scal + (size_t)b * sbec::S_COUNT; }
+
+    // scalars of every instance; per-instance device statuses go to dstat and are cleared
+    int pull() {
+        const size_t n = (size_t)B * sbec::S_COUNT;
+        if (cudaMemcpyAsync(h->h_scal, w.scal, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            dstat[b] = (int)hs(b)[SBEC_S_STATUS];
+            if (dstat[b]) { any = true; hs(b)[SBEC_S_STATUS] = 0.0; }
+            if (dstat[b] && dstat[b] != SBEC_ERR_DOMAIN) return dstat[b];
+        }
+        return any ? push() : SBEC_OK;
+    }
+    // host-written parameter slots back to the device (the block is in sync after pull)
+    int push() {
+        const size_t n = (size_t)B * sbec::S_COUNT;
+        if (cudaMemcpyAsync(w.scal, h->h_scal, n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+        return SBEC_OK;
+    }
+
+    int lin(void* out, double ca, const void* A, double cb, const void* Bv, int ib = -1, int guard = -1,
+            const void* D1 = nullptr, const void* D2 = nullptr, int slot = SL_D0) {
+        Lin L;
+        L.out = out; L.A = A; L.B = Bv; L.ca = ca; L.cb = cb; L.ia = -1; L.ib = ib; L.ineg = -1;
+        L.D1 = D1; L.D2 = D2; L.guard = guard;
+        return Ops<T>::lincomb(g, w, L, slot, s);
+    }
+    int grad(const void* u, void* gE, void* rg) {
+        for (int b = 0; b < B; ++b) ++st[b].n_grad;
+        return Ops<T>::grad(g, w, u, gE, rg, true, s);
+    }
+    int energy(const void* x) {
+        for (int b = 0; b < B; ++b) ++st[b].n_energy;
+        return Ops<T>::energy(g, w, x, s);
+    }
+
+#define TRY(x) do { int e_ = (x); if (e_) return e_; } while (0)
+
+    int rgbb(void* u, void* up, void* z, void* rg, void* rgp, double tol, long long maxit, std::vector<double>& E,
+             std::vector<double>& gn, std::vector<char>& act) {
+        TRY(energy(u));
+        TRY(pull());
+        std::vector<double> Ck(B), Qk(B, 1.0), t(B), slope(B), Ez(B);
+        std::vector<char> tr(B);
+        for (int b = 0; b < B; ++b) { E[b] = hs(b)[SBEC_S_ENERGY]; Ck[b] = E[b]; }
+        bool have_prev = false;
+        for (long long k = 0; k <= maxit; ++k) {
+            TRY(grad(u, nullptr, rg));
+            if (have_prev) TRY(Ops<T>::bbdots(g, w, u, up, rg, rgp, SL_D0, s));
+            TRY(pull());
+            bool any = false;
+            for (int b = 0; b < B; ++b) {
+                gn[b] = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]);
+                if (act[b] && (gn[b] <= tol || k == maxit)) act[b] = 0;
+                any = any || act[b];
+            }
+            if (!any) return SBEC_OK;
+            for (int b = 0; b < B; ++b) {
+                double gam = 1e-3;
+                if (have_prev) {
+                    const double sv = hs(b)[SL_D0], vv = hs(b)[SL_D0 + 1];
+                    gam = vv > 0.0 ? fabs(sv) / vv : 1e-3;
+                    gam = fmin(fmax(gam, 1e-10), 1e10);
+                }
+                t[b] = gam;
+                slope[b] = -gn[b] * gn[b];
+                tr[b] = act[b];
+                Ez[b] = INFINITY;
+            }
+            for (int bt = 0; bt <= 10; ++bt) {
+                for (int b = 0; b < B; ++b) hs(b)[SL_T] = act[b] ? -t[b] : 0.0;
+                TRY(push());
+                TRY(Ops<T>::retract(g, w, u, rg, 1.0, o.retraction, z, s, SL_T));
+                TRY(energy(z));
+                TRY(pull());
+                bool more = false;
+                for (int b = 0; b < B; ++b) {
+                    if (!tr[b]) continue;
+                    Ez[b] = dstat[b] == SBEC_ERR_DOMAIN ? INFINITY : hs(b)[SBEC_S_ENERGY];
+                    if (Ez[b] <= Ck[b] + 1e-4 * t[b] * slope[b]) tr[b] = 0;
+                    else if (bt < 10) t[b] *= 0.2;
+                    more = more || tr[b];
+                }
+                if (!more) break;
+            }
+            for (int b = 0; b < B; ++b) {
+                if (act[b] && !isfinite(Ez[b])) act[b] = 0;       // no admissible trial: stop this instance
+                hs(b)[SL_ACT] = act[b] ? 1.0 : 0.0;
+            }
+            TRY(push());
+            TRY(lin(up, 1.0, u, 0.0, nullptr, -1, SL_ACT));
+            TRY(lin(rgp, 1.0, rg, 0.0, nullptr, -1, SL_ACT));
+            TRY(lin(u, 1.0, z, 0.0, nullptr, -1, SL_ACT));
+            for (int b = 0; b < B; ++b) {
+                if (!act[b]) continue;
+                E[b] = Ez[b];
+                const double Qn = 0.85 * Qk[b] + 1.0;
+                Ck[b] = (0.85 * Qk[b] * Ck[b] + E[b]) / Qn;
+                Qk[b] = Qn;
+                ++st[b].rgbb_iters;
+            }
+            have_prev = true;
+        }
+        return SBEC_OK;
+    }
+
+    int arnt(void* u, void* z, void* gE, void* rg, void* x, void* r, void* p, void* Hp, double tol, long long maxit,
+             std::vector<double>& E, std::vector<double>& gn) {
+        TRY(energy(u));
+        TRY(pull());
+        for (int b = 0; b < B; ++b) E[b] = hs(b)[SBEC_S_ENERGY];
+        std::vector<double> sig_hat(B, 1.0), sig_floor(B, 0.0), sigma(B), rr(B), stop(B), sest(B), beta(B), t(B),
+            slope(B), mz(B), Ez(B);
+        std::vector<int> maxin(B), jj(B);
+        std::vector<char> act(B), cg(B), neg(B), hd(B), ls(B);
+        TRY(grad(u, gE, rg));
+        TRY(pull());
+        for (int b = 0; b < B; ++b) { gn[b] = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]); act[b] = 1; }
+        for (long long k = 0; k <= maxit; ++k) {
+            bool any = false;
+            for (int b = 0; b < B; ++b) {
+                if (act[b] && (gn[b] <= tol || k == maxit)) act[b] = 0;
+                any = any || act[b];
+            }
+            if (!any) break;
+            for (int b = 0; b < B; ++b) {
+                sigma[b] = fmax(sig_hat[b] * gn[b], sig_floor[b]);
+                maxin[b] = gn[b] > 1e-3 ? 100 : 300;
+                stop[b] = fmin(0.1, gn[b]) * gn[b];
+                hs(b)[SL_SIG] = sigma[b];
+            }
+            // ---- modified CG, lock-step over the instances still in it ----
+            TRY(lin(x, 0.0, rg, 0.0, nullptr));
+            TRY(lin(r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
+            TRY(lin(p, 1.0, r, 0.0, nullptr));
+            TRY(pull());
+            bool incg = false;
+            for (int b = 0; b < B; ++b) {
+                rr[b] = hs(b)[SL_RRA];
+                cg[b] = act[b] && rr[b] > 0.0;
+                jj[b] = 0; neg[b] = 0; hd[b] = 0; sest[b] = -1.0;
+                incg = incg || cg[b];
+            }
+            int parity = 0;
+            while (incg) {
+                const int rr_now = parity ? SL_RRB : SL_RRA, rr_next = parity ? SL_RRA : SL_RRB;
+                for (int b = 0; b < B; ++b) { hs(b)[SL_CG] = cg[b] ? 1.0 : 0.0; hs(b)[SL_SIG] = sigma[b]; }
+                TRY(push());
+                for (int b = 0; b < B; ++b) ++st[b].n_hvp;
+                TRY(Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, s, SL_SIG));
+                TRY(Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, s));
+                TRY(Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s, SL_CG));
+                TRY(lin(x, 1.0, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1));
+                TRY(lin(r, 1.0, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, nullptr, rr_next));
+                TRY(pull());
+                incg = false;
+                for (int b = 0; b < B; ++b) {
+                    if (!cg[b]) continue;
+                    ++jj[b];
+                    ++st[b].inner_iters;
+                    const double kap = hs(b)[SL_KAP], pp = hs(b)[SL_KAP + 1], rrn = hs(b)[rr_next];
+                    if (kap <= 1e-12 * pp) {
+                        sest[b] = fabs(kap) / pp;
+                        if (jj[b] == 1) neg[b] = 1;
+                        else if (kap < -1e-12 * pp) hd[b] = 1;
+                        cg[b] = 0;
+                    } else if (sqrt(rrn) <= stop[b]) {
+                        cg[b] = 0;
+                    } else {
+                        beta[b] = rrn / rr[b];
+                        rr[b] = rrn;
+                        if (jj[b] >= maxin[b]) cg[b] = 0;
+                    }
+                    incg = incg || cg[b];
+                }
+                for (int b = 0; b < B; ++b) {
+                    hs(b)[SL_CG] = cg[b] ? 1.0 : 0.0;
+                    hs(b)[SL_BETA] = cg[b] ? beta[b] : 0.0;
+                }
+                TRY(push());
+                if (incg) TRY(lin(p, 1.0, r, 1.0, p, SL_BETA, SL_CG));
+                parity ^= 1;
+            }
+            // ---- xi (Eq. xi) into x ----
+            bool anyneg = false, anyhd = false;
+            for (int b = 0; b < B; ++b) {
+                hs(b)[SL_NEG] = (act[b] && neg[b]) ? 1.0 : 0.0;
+                anyneg = anyneg || (act[b] && neg[b]);
+                anyhd = anyhd || (act[b] && hd[b]);
+            }
+            TRY(push());
+            if (anyneg) TRY(lin(x, -1.0, rg, 0.0, nullptr, -1, SL_NEG));
+            if (anyhd) {
+                TRY(Ops<T>::dot2(g, w, p, rg, p, Hp, SL_D0, s));
+                TRY(pull());
+                for (int b = 0; b < B; ++b) {
+                    const bool on = act[b] && hd[b];
+                    hs(b)[SL_HD] = on ? 1.0 : 0.0;
+                    hs(b)[SL_TAU] = on ? hs(b)[SL_D0] / hs(b)[SL_D0 + 1] : 0.0;
+                }
+                TRY(push());
+                TRY(lin(x, 1.0, x, 1.0, p, SL_TAU, SL_HD));
+            }
+            TRY(Ops<T>::dot2(g, w, rg, x, nullptr, nullptr, SL_D0, s));
+            TRY(pull());
+            bool anyfix = false;
+            for (int b = 0; b < B; ++b) {
+                slope[b] = hs(b)[SL_D0];
+                const bool fix = act[b] && (!(slope[b] < 0.0) || !isfinite(slope[b]));
+                hs(b)[SL_NEG] = fix ? 1.0 : 0.0;
+                if (fix) slope[b] = -gn[b] * gn[b];
+                anyfix = anyfix || fix;
+            }
+            if (anyfix) {
+                TRY(push());
+                TRY(lin(x, -1.0, rg, 0.0, nullptr, -1, SL_NEG));
+            }
+            // ---- curvilinear search, lock-step ----
+            const double eps = sizeof(T) == 8 ? kEps : 1.1920928955078125e-07;
+            for (int b = 0; b < B; ++b) { t[b] = 1.0; ls[b] = act[b]; mz[b] = INFINITY; }
+            for (int bt = 0; bt <= 10; ++bt) {
+                for (int b = 0; b < B; ++b) hs(b)[SL_T] = act[b] ? t[b] : 0.0;
+                TRY(push());
+                TRY(Ops<T>::retract(g, w, u, x, 1.0, o.retraction, z, s, SL_T));
+                TRY(lin(r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));
+                for (int b = 0; b < B; ++b) ++st[b].n_hvp;
+                TRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s));
+                TRY(Ops<T>::dot2(g, w, r, Hp, nullptr, nullptr, SL_MB, s));
+                TRY(pull());
+                bool more = false;
+                for (int b = 0; b < B; ++b) {
+                    if (!ls[b]) continue;
+                    const double noise = 100.0 * eps * fmax(1.0, fabs(E[b]));
+                    mz[b] = dstat[b] == SBEC_ERR_DOMAIN
+                                ? INFINITY
+                                : hs(b)[SL_MA] + 0.5 * hs(b)[SL_MB] + 0.5 * sigma[b] * hs(b)[SL_MA + 1];
+                    if (mz[b] <= 1e-4 * t[b] * slope[b] || fabs(mz[b]) <= noise) ls[b] = 0;
+                    else if (bt < 10) t[b] *= 0.2;
+                    more = more || ls[b];
+                }
+                if (!more) break;
+            }
+            TRY(energy(z));
+            TRY(pull());
+            bool anyacc = false;
+            for (int b = 0; b < B; ++b) {
+                bool acc = false;
+                if (act[b]) {
+                    Ez[b] = dstat[b] == SBEC_ERR_DOMAIN ? INFINITY : hs(b)[SBEC_S_ENERGY];
+                    const double noise = 100.0 * eps * fmax(1.0, fabs(E[b]));
+                    double ratio;
+                    if (fabs(mz[b]) <= noise && fabs(Ez[b] - E[b]) <= noise) ratio = 1.0;
+                    else ratio = (mz[b] < 0.0 && isfinite(Ez[b])) ? (Ez[b] - E[b]) / mz[b] : -1.0;
+                    acc = ratio >= 0.01;
+                    if (acc) { E[b] = Ez[b]; sig_hat[b] *= (ratio >= 0.9) ? 0.2 : 1.0; }
+                    else sig_hat[b] *= 10.0;
+                    sig_floor[b] = sest[b] >= 0.0 ? sest[b] : 0.0;
+                    ++st[b].outer_iters;
+                }
+                hs(b)[SL_ACC] = acc ? 1.0 : 0.0;
+                anyacc = anyacc || acc;
+            }
+            TRY(push());
+            if (anyacc) {
+                TRY(lin(u, 1.0, z, 0.0, nullptr, -1, SL_ACC));
+                TRY(grad(u, gE, rg));
+                TRY(pull());
+                for (int b = 0; b < B; ++b) gn[b] = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]);
+            }
+            for (int b = 0; b < B; ++b)
+                if (act[b] && sig_hat[b] > 1e20) act[b] = 0;
+        }
+        return SBEC_OK;
+    }
+
+    int run(void* Xdev) {
+        void *u = f[0], *up = f[1], *z = f[2], *gE = f[3], *rg = f[4], *rgp = f[5];
+        if (cudaMemcpyAsync(u, Xdev, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
+        if (o.project_initial) {
+            TRY(Ops<T>::retract(g, w, u, u, 0.0, 1, u, s));
+            TRY(pull());
+            for (int b = 0; b < B; ++b)
+                if (dstat[b]) return SBEC_ERR_DOMAIN;
+        }
+        std::vector<double> E(B, 0.0), gn(B, INFINITY);
+        std::vector<char> act(B, 1);
+        if (o.method == SBEC_RGBB) {
+            TRY(rgbb(u, up, z, rg, rgp, o.tol, o.maxit, E, gn, act));
+        } else {
+            TRY(rgbb(u, up, z, rg, rgp, fmax(o.tol, o.rgbb_tol), o.rgbb_maxit, E, gn, act));
+            bool any = false;
+            for (int b = 0; b < B; ++b) any = any || gn[b] > o.tol;
+            if (any) TRY(arnt(u, z, gE, rg, f[6], f[7], f[8], f[9], o.tol, o.maxit, E, gn));
+        }
+        TRY(grad(u, nullptr, rg));
+        TRY(pull());
+        bool all = true;
+        for (int b = 0; b < B; ++b) {
+            st[b].energy = hs(b)[SBEC_S_ENERGY];
+            st[b].grad_norm = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]);
+            st[b].converged = st[b].grad_norm <= o.tol;
+            all = all && st[b].converged;
+        }
+        if (cudaMemcpyAsync(Xdev, u, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SBEC_ERR_CUDA;
+        return all ? SBEC_OK : SBEC_ERR_NOCONV;
+    }
+#undef TRY
+};
+
 }  // namespace
 
 extern "C" {
@@ -289,6 +643,27 @@ void sbec_solve_defaults(sbec_solve_opts* o) {
     o->rgbb_tol = 1e-2;
     o->rgbb_maxit = 2000;
     o->project_initial = 1;
+}
+
+int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+                     sbec_stats* stats) {
+    if (!h || !X || !workspace || !stats) return SBEC_ERR_ARG;
+    if (workspace_bytes < 10 * h->field_bytes || !sbec_is_device_ptr(workspace) || !sbec_is_device_ptr(X))
+        return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    if (o.retraction < 1 || o.retraction > 3 || !(o.tol > 0.0) || o.maxit < 0 || o.rgbb_maxit < 0) return SBEC_ERR_ARG;
+    memset(stats, 0, sizeof(sbec_stats) * (size_t)h->B);
+    int rc;
+    if (h->prob.precision == SBEC_FP64) {
+        BatchSolver<double> S(h, o, workspace, stats);
+        rc = S.run(X);
+    } else {
+        BatchSolver<float> S(h, o, workspace, stats);
+        rc = S.run(X);
+    }
+    h->last_grad_X = nullptr;
+    return rc;
 }
 
 int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes) {

@@ -403,3 +403,28 @@ def solve_cascadic(handles, states, tol=1e-8, tol_coarse=1e-5, method="arnt", re
     out = {k: getattr(st, k) for k, _ in Stats._fields_}
     out["status"] = rc
     return out
+
+
+_lib.sbec_solve_batch.argtypes = [_vp, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.c_size_t, ctypes.POINTER(Stats)]
+_lib.sbec_solve_batch.restype = _int
+
+
+def solve_batch(h, X, tol=1e-8, method="arnt", retraction=1, maxit=10000, rgbb_tol=1e-2, rgbb_maxit=2000,
+                project=True, workspace=None):
+    """Lock-step ground-state solve of every instance of a batch handle (sbec_solve_batch).
+    X: device tensor (B, C, ...), overwritten.  Returns a list of per-instance stats dicts."""
+    o = SolveOpts()
+    _lib.sbec_solve_defaults(ctypes.byref(o))
+    o.method = ARNT if method == "arnt" else RGBB
+    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
+    o.rgbb_tol, o.rgbb_maxit, o.project_initial = float(rgbb_tol), int(rgbb_maxit), int(bool(project))
+    nb = ctypes.c_size_t()
+    _check(_lib.sbec_solve_workspace_bytes(h._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
+    if workspace is None:
+        import torch
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    st = (Stats * h.B)()
+    rc = _lib.sbec_solve_batch(h._h, _ptr(X), ctypes.byref(o), _ptr(workspace), nb.value, st)
+    if rc not in (OK, ERR_NOCONV):
+        _check(rc, "sbec_solve_batch")
+    return [dict({k: getattr(st[i], k) for k, _ in Stats._fields_}, status=rc) for i in range(h.B)]

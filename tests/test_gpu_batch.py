@@ -80,3 +80,21 @@ def test_batch_of_one_equals_single_handle(dev):
         b = hb.grad(X, G_riem=G2)
     assert a == b
     assert torch.equal(G1, G2)
+
+
+@pytest.mark.parametrize("F,n,L,count", [(1, (64,), 8.0, 4), (1, (16, 16), 6.0, 3)])
+def test_batch_solve_matches_oracle_per_instance(F, n, L, count, dev):
+    # a14: many instances with their own beta and M solved together (lock step)
+    from paper_1907_01194_gb300 import sbec
+    ws = _batch(F, n, L, count, seed=5)
+    X0 = np.stack([W.initial_fields(w) for w in ws])
+    X = torch.from_numpy(X0).to(dev)
+    with sbec.Handle.batch(ws) as h:
+        sts = sbec.solve_batch(h, X, tol=1e-9)
+    for i, w in enumerate(ws):
+        P = O.Problem(F=w.F, n=w.n, lo=w.lo, hi=w.hi, beta=w.beta, V=W.potential(w), M=w.M)
+        Xs, ost, _ = O.solve(P, O.to_matrix(P, X0[i]), O.SolveOptions(tol=1e-9))
+        assert sts[i]["converged"] and ost.converged
+        assert abs(sts[i]["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+        m = np.sum(np.abs(X[i].cpu().numpy().reshape(w.C, -1)) ** 2, axis=1)
+        assert abs(m.sum() - 1) < 1e-12 and abs(m @ np.arange(w.F, -w.F - 1, -1) - w.M) < 1e-12
