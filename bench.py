@@ -1,18 +1,21 @@
 """Benchmark of the spin-F BEC hot path on one (or N replicated) GB300.
 
-Workload: spin-2, 2D, 256 x 256 on [-12,12]^2, V = |x|^2/2 + 20 sum sin^2(pi x_i/2),
-beta = (200, 10, -5), M = 0.3 (synthetic; seeded Gaussian-times-noise states put on
-the constraint manifold by the library's own projective retraction).
+Default workload: spin-2, 2D, 256 x 256 on [-12,12]^2, V = |x|^2/2 + 20 sum sin^2(pi x_i/2),
+beta = (200, 10, -5), M = 0.3 (synthetic; seeded Gaussian-times-noise states put on the
+constraint manifold by the library's own projective retraction).  `--workload` selects
+the other synthetic workloads: spin1_1d (n = 256), spin3_3d_128 (the finest level of the
+32^3 -> 64^3 -> 128^3 cascadic workload), spin3_3d_256, batch512 (512 spin-1 2D instances
+on 64^2 / 128^2 / 256^2 grids with their own beta1 and M).
 
 One step = one pass of the hot path as a Newton/BB iteration uses it:
   sbec_grad     energy, Euclidean and Riemannian gradient, ||grad E|| (Eq. 3.7, 3.12, Lemma 4.1)
   sbec_hessvec  Riemannian Hessian-vector product along the gradient (Eq. 3.13, Lemma 4.2)
   sbec_retract  projective retraction of a trial step (Lemma 5.1)
   sbec_energy   energy of the trial point
-Each step works on a different one of 32 resident states (168 MB > the 129 MB L2),
-so no step reads its inputs from L2 left by the previous one.
+Each step works on a different resident state, with enough states that they exceed the
+129 MB L2, so no step reads its inputs from L2 left by the previous one.
 
-metric value = energy+grad evaluations per second (one per step) over all ranks.
+metric value = energy+grad evaluations per second (one per step and instance) over all ranks.
 `--impl reference` times the CPU FP64 oracle doing the same step.
 """
 from __future__ import annotations
@@ -39,17 +42,21 @@ from paper_1907_01194_gb300 import workloads as W  # noqa: E402
 
 METRIC = "energy+grad evals/s and time-to-ground-state (|Rgrad|<1e-8), % HBM roofline"
 UNIT = "evals/s"
-NSTATES = 32
 T_TRIAL = 1e-3
 SIGMA = 0.5
+L2_BYTES = 129e6
 
 # FP64 ALU peak: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (the recipe's unit counts and
 # maximum SM clock); the FMA probe measured 1.195 TFLOP/s on this machine's GB300.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+HBM_PEAK_GBS = 6794.5          # MEASURED_PEAKS.json hbm_gbs (copy, read + write)
 # pointwise FLOPs per grid point of the epilogues (counted from Eq. 3.7, 3.12, 3.13 in the
 # ladder / pair form the kernels use; the derivation is in the design doc)
 PW_FLOPS = {"grad": {1: 170, 2: 375, 3: 760}, "hess": {1: 300, 2: 640, 3: 1400},
             "energy": {1: 70, 2: 140, 3: 290}}
+# DRAM traffic per launch from ncu captures of the unchanged kernels (bytes), by
+# (kernel, workload); profiles/ holds the summaries
+NCU_TRAFFIC = {("x_inv_hess", "spin2_2d_256x256"): 16321792.0}
 
 
 def parse():
@@ -58,6 +65,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="spin2_2d",
+                    choices=["spin1_1d", "spin2_2d", "spin3_3d_128", "spin3_3d_256", "batch512"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-ground-state solves")
     return ap.parse_args()
@@ -70,8 +80,20 @@ def dist_setup():
     return world, rank, local
 
 
-def workload():
-    return W.spin2_2d()
+def workload(name):
+    if name == "spin1_1d":
+        return W.spin1_1d()
+    if name == "spin2_2d":
+        return W.spin2_2d()
+    if name == "spin3_3d_128":
+        return W.spin3_3d_cascadic()
+    if name == "spin3_3d_256":
+        return W.spin3_3d_256()
+    raise ValueError(name)
+
+
+def solve_tol(name):
+    return 1e-10 if name == "spin1_1d" else 1e-8
 
 
 # ---------------------------------------------------------------------------
@@ -93,22 +115,22 @@ def oracle_step_runner(w):
     return step
 
 
+def cpu_sample(w, budget=15.0, max_steps=50):
+    step = oracle_step_runner(w)
+    step()
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps and (n == 0 or time.perf_counter() - t0 < budget):
+        step()
+        n += 1
+    return n, time.perf_counter() - t0
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    w = workload()
-    step = oracle_step_runner(w)
-    for _ in range(max(1, min(args.warmup, 1))):
-        step()
-    t0 = time.perf_counter()
-    n = 0
-    budget = 120.0
-    while n < args.steps:
-        step()
-        n += 1
-        if time.perf_counter() - t0 > budget:
-            break
-    dt = time.perf_counter() - t0
+    w = W.batched_spin1_2d()[2] if args.workload == "batch512" else workload(args.workload)
+    n, dt = cpu_sample(w, budget=120.0, max_steps=args.steps)
     val = n / dt
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
@@ -178,36 +200,60 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def flops_model(w, kname, launches):
-    """Algorithmic FLOPs of one launch kind (per launch) for the workload."""
+def flops_model(w, kname, B=1):
+    """Algorithmic FLOPs of one launch kind (per launch) for the workload (B instances)."""
     C, n = w.C, w.n
     G = int(np.prod(n))
     fft = lambda m: 5.0 * m * math.log2(m)
+    d = len(n)
     if kname == "s_k2":
         m = n[-1]
-        return C * (G // m) * (2 * fft(m) + 4 * m)
-    if kname in ("s_fwd", "s_inv", "s_parseval"):
-        m = n[1]
-        return C * (G // m) * fft(m)
+        return B * C * (G // m) * (2 * fft(m) + 4 * m)
+    if kname in ("s_fwd", "s_inv", "s_parseval") and d > 1:
+        m = n[1] if kname != "s_parseval" else n[-1]
+        return B * C * (G // m) * fft(m)
     if kname == "x_fwd":
-        return C * (G // n[0]) * fft(n[0])
+        return B * C * (G // n[0]) * fft(n[0])
     if kname == "x_fwd_energy":
-        return C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["energy"][w.F]
+        return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["energy"][w.F])
     if kname == "x_inv_grad":
-        return C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["grad"][w.F]
+        return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["grad"][w.F])
     if kname == "x_inv_hess":
-        return C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["hess"][w.F]
+        return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["hess"][w.F])
+    if kname == "x_full_grad":
+        return B * (C * (2 * fft(n[0]) + 4 * n[0]) + G * PW_FLOPS["grad"][w.F])
+    if kname == "x_full_hess":
+        return B * (C * (2 * fft(n[0]) + 4 * n[0]) + G * PW_FLOPS["hess"][w.F])
     return None
 
 
-def bytes_model(w, kname, elem):
-    """Algorithmic DRAM bytes of one launch (compulsory reads + writes)."""
+def bytes_model(w, kname, elem, B=1):
+    """Compulsory DRAM bytes of one launch (reads + writes), elem = bytes per complex value."""
     C, G = w.C, int(np.prod(w.n))
-    S = C * G * elem
-    SV = G * elem // 2
+    S = B * C * G * elem
+    SV = B * G * elem // 2
     return {"x_fwd": 2 * S, "x_fwd_energy": 2 * S + SV, "s_k2": 2 * S, "s_fwd": 2 * S, "s_inv": 2 * S,
-            "s_parseval": S, "x_inv_grad": 3 * S + SV, "x_inv_hess": 4 * S + SV,
-            "proj_apply": 3 * S, "dot_reduce": 2 * S, "retract_w": 3 * S, "scale": 2 * S}.get(kname)
+            "s_parseval": S, "x_inv_grad": 3 * S + SV, "x_inv_hess": 4 * S + SV, "x_full_grad": 3 * S + SV,
+            "x_full_hess": 4 * S + SV, "proj_apply": 3 * S, "dot_reduce": 2 * S, "retract_w": 3 * S,
+            "scale": 2 * S, "lincomb": 3 * S}.get(kname)
+
+
+def roofline_of(prof, w, precision, B, wname):
+    total = sum(v[0] for v in prof.values())
+    kname, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_s = kms / kcnt * 1e-3
+    if precision == "fp64":
+        fl = flops_model(w, kname, B)
+        ach = fl / per_launch_s / 1e9 if fl else None
+        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PEAK_GFLOPS if ach else None,
+                "traffic": NCU_TRAFFIC.get((kname, wname)), "kernel": kname, "kernel_share": kms / total,
+                "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
+    by = bytes_model(w, kname, 8, B)
+    ach = by / per_launch_s / 1e9 if by else None
+    return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": ach / HBM_PEAK_GBS if ach else None, "traffic": NCU_TRAFFIC.get((kname, wname)),
+            "kernel": kname, "kernel_share": kms / total, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
 
 
 def run_ours(args, world, rank, local):
@@ -227,31 +273,62 @@ def run_ours(args, world, rank, local):
             pg.barrier()
         torch.cuda.synchronize()
 
-    w = workload()
-    stream = torch.cuda.current_stream()
-    h = sbec.Handle.from_workload(w, precision="fp64", stream=stream.cuda_stream)
-    states = []
-    for i in range(NSTATES):
-        X = torch.from_numpy(W.initial_fields(w, seed=w.seed + 97 * i)).to(dev)
-        h.retract(X, torch.zeros_like(X), 0.0, 1, X)     # put it on the manifold (R1 of u)
-        states.append(X)
-    h.sync()
-    RG = torch.empty_like(states[0])
-    HZ = torch.empty_like(states[0])
-    XT = torch.empty_like(states[0])
+    def max_over_ranks(x):
+        if not pg:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
 
-    def step(k, hh=h, st=states, rg=RG, hz=HZ, xt=XT):
-        X = st[k % len(st)]
-        hh.grad(X, G_riem=rg, sync=False)
-        hh.hessvec(X, rg, hz, sigma=SIGMA, riemannian=True)
-        hh.retract(X, rg, -T_TRIAL, 1, xt)
-        hh.energy(xt, sync=False)
+    stream = torch.cuda.current_stream()
+    cdt = torch.complex128 if args.precision == "fp64" else torch.complex64
+    elem = 16 if args.precision == "fp64" else 8
+
+    # ---- handles and resident states ----
+    if args.workload == "batch512":
+        insts = W.batched_spin1_2d()
+        groups = []
+        for n in (64, 128, 256):
+            ws = [w for w in insts if w.n[0] == n]
+            h = sbec.Handle.batch(ws, precision=args.precision, stream=stream.cuda_stream)
+            X = torch.from_numpy(np.stack([W.initial_fields(w) for w in ws])).to(dev).to(cdt)
+            h.retract(X, torch.zeros_like(X), 0.0, 1, X)
+            groups.append((h, [X], ws))
+        wname = "batch512_spin1_2d_64_128_256"
+        w_main = insts[2]
+        n_inst = len(insts)
+        nstates = 1
+    else:
+        w_main = workload(args.workload)
+        wname = w_main.name
+        h = sbec.Handle.from_workload(w_main, precision=args.precision, stream=stream.cuda_stream)
+        sbytes = w_main.C * w_main.G * elem
+        nstates = int(min(32, max(1, math.ceil(2 * L2_BYTES / sbytes))))
+        states = []
+        for i in range(nstates):
+            X = torch.from_numpy(W.initial_fields(w_main, seed=w_main.seed + 97 * i)).to(dev).to(cdt)
+            h.retract(X, torch.zeros_like(X), 0.0, 1, X)     # put it on the manifold (R1 of u)
+            states.append(X)
+        groups = [(h, states, [w_main])]
+        n_inst = 1
+    for h, st, _ in groups:
+        h.sync()
+    bufs = [tuple(torch.empty_like(st[0]) for _ in range(3)) for _, st, _ in groups]
+
+    def step(k):
+        for (hh, st, _), (rg, hz, xt) in zip(groups, bufs):
+            X = st[k % len(st)]
+            hh.grad(X, G_riem=rg, sync=False)
+            hh.hessvec(X, rg, hz, sigma=SIGMA, riemannian=True)
+            hh.retract(X, rg, -T_TRIAL, 1, xt)
+            hh.energy(xt, sync=False)
 
     for k in range(args.warmup):
         step(k)
-    h.sync()
+    for h, _, _ in groups:
+        h.sync()
     barrier()
-    n0 = h.launch_count()
+    n0 = sum(h.launch_count() for h, _, _ in groups)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
@@ -260,46 +337,53 @@ def run_ours(args, world, rank, local):
         ev1.record(stream)
         ev1.synchronize()
     barrier()
-    launches = h.launch_count() - n0
-    ms = ev0.elapsed_time(ev1)
-    status = h.sync_status()
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms * 1e-3)
+    launches = sum(h.launch_count() for h, _, _ in groups) - n0
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    status = max(h.sync_status() for h, _, _ in groups)
+    value = world * n_inst * args.steps / (ms * 1e-3)
     clocks = clk.summary()
 
     # per-kernel device times (separate pass with event timing around every launch)
-    h.profile(True)
+    for h, _, _ in groups:
+        h.profile(True)
     for k in range(args.steps):
         step(k)
-    prof = h.profile_read()
-    h.profile(False)
-    total = sum(v[0] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1][0])
-    kname, (kms, kcnt) = top
-    per_launch_s = kms / kcnt * 1e-3
-    fl = flops_model(w, kname, kcnt)
-    roofline = {"bound": "alu", "achieved": fl / per_launch_s / 1e9 if fl else None,
-                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": (fl / per_launch_s / 1e9) / FP64_PEAK_GFLOPS if fl else None,
-                "traffic": None, "kernel": kname, "kernel_share": kms / total,
-                "peak_source": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz"}
+    prof = {}
+    for h, _, _ in groups:
+        for kname, (kms, kcnt) in h.profile_read().items():
+            a = prof.get(kname, (0.0, 0))
+            prof[kname] = (a[0] + kms, a[1] + kcnt)
+        h.profile(False)
+    if args.workload == "batch512":
+        # roofline of the largest size class (170 instances of 256^2), profiled alone
+        hh, st, _ = groups[-1]
+        rg, hz, xt = bufs[-1]
+        hh.profile(True)
+        for k in range(args.steps):
+            hh.grad(st[0], G_riem=rg, sync=False)
+            hh.hessvec(st[0], rg, hz, sigma=SIGMA, riemannian=True)
+            hh.retract(st[0], rg, -T_TRIAL, 1, xt)
+            hh.energy(xt, sync=False)
+        prof_last = hh.profile_read()
+        hh.profile(False)
+        roofline = roofline_of(prof_last, w_main, args.precision, hh.B, wname)
+    else:
+        roofline = roofline_of(prof, w_main, args.precision, 1, wname)
 
     # end-to-end through the C ABI with pinned host buffers: every call takes host
     # arrays, so the library copies inputs in and results out on its stream
-    hostX = [torch.empty(states[0].shape, dtype=states[0].dtype).pin_memory() for _ in range(4)]
+    hh, st, _ = groups[-1]
+    hostX = [torch.empty(st[0].shape, dtype=st[0].dtype).pin_memory() for _ in range(min(4, len(st)))]
     for i, hx in enumerate(hostX):
-        hx.copy_(states[i].cpu())
+        hx.copy_(st[i].cpu())
     hRG, hHZ, hXT = (torch.empty_like(hostX[0]).pin_memory() for _ in range(3))
 
     def e2e_step(k):
-        hx = hostX[k % 4]
-        h.grad(hx, G_riem=hRG)                            # H2D X; D2H grad E, |grad|, E
-        h.hessvec(hx, hRG, hHZ, sigma=SIGMA, riemannian=True)   # H2D X, Z; D2H HZ
-        h.retract(hx, hRG, -T_TRIAL, 1, hXT)              # H2D U, Xi; D2H trial point
-        return h.energy(hXT)                              # H2D trial point; D2H E
+        hx = hostX[k % len(hostX)]
+        hh.grad(hx, G_riem=hRG)                           # H2D X; D2H grad, |grad|, E
+        hh.hessvec(hx, hRG, hHZ, sigma=SIGMA, riemannian=True)   # H2D X, Z; D2H HZ
+        hh.retract(hx, hRG, -T_TRIAL, 1, hXT)             # H2D U, Xi; D2H trial point
+        return hh.energy(hXT)                             # H2D trial point; D2H E
 
     for k in range(2):
         e2e_step(k)
@@ -309,97 +393,149 @@ def run_ours(args, world, rank, local):
     for k in range(ne):
         e2e_step(k)
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_dt], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = max_over_ranks(time.perf_counter() - t0)
     nbytes = hostX[0].numel() * hostX[0].element_size()
-    e2e = {"value": world * ne / e2e_dt, "unit": UNIT,
-           "h2d_bytes_per_step": 6 * nbytes, "d2h_bytes_per_step": 3 * nbytes + 3 * 16}
+    e2e = {"value": world * hh.B * ne / e2e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": 6 * nbytes, "d2h_bytes_per_step": 3 * nbytes + 3 * 16 * hh.B,
+           "scope": "largest size class" if args.workload == "batch512" else "workload"}
 
-    # mixed form (FP32 FFT and pointwise, FP64 reductions) on the same step
-    hm = sbec.Handle.from_workload(w, precision="mixed", stream=stream.cuda_stream)
-    mstates = [s.to(torch.complex64) for s in states]
-    mRG, mHZ, mXT = (torch.empty_like(mstates[0]) for _ in range(3))
-    for k in range(args.warmup):
-        step(k, hm, mstates, mRG, mHZ, mXT)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for k in range(args.steps):
-        step(k, hm, mstates, mRG, mHZ, mXT)
-    ev1.record(stream)
-    ev1.synchronize()
-    mixed_value = world * args.steps / (ev0.elapsed_time(ev1) * 1e-3)
-    hm.close()
+    # mixed form on the same step (when the headline is FP64)
+    mixed_value = None
+    if args.precision == "fp64" and args.workload != "batch512":
+        hm = sbec.Handle.from_workload(w_main, precision="mixed", stream=stream.cuda_stream)
+        mst = [x.to(torch.complex64) for x in groups[0][1]]
+        mb = tuple(torch.empty_like(mst[0]) for _ in range(3))
+        save = groups[:], bufs[:]
+        groups[:] = [(hm, mst, [w_main])]
+        bufs[:] = [mb]
+        for k in range(args.warmup):
+            step(k)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            step(k)
+        ev1.record(stream)
+        ev1.synchronize()
+        mixed_value = world * args.steps / (ev0.elapsed_time(ev1) * 1e-3)
+        groups[:], bufs[:] = save
+        hm.close()
 
-    # time to ground state (|Rgrad| < 1e-8) from the seeded initial state: FP64 ARNT, and
-    # the mixed form (FP32 FFT / pointwise to 1e-3) followed by FP64 refinement
+    # time to ground state from the seeded initial state
     tts = None
-    if not args.no_solve:
-        X0 = torch.from_numpy(W.initial_fields(w)).to(dev)
-        nb64 = 10 * X0.numel() * 16
-        ws = torch.empty(nb64 + 11 * X0.numel() * 8, dtype=torch.uint8, device=dev)
-        hm2 = sbec.Handle.from_workload(w, precision="mixed", stream=stream.cuda_stream)
-        X = X0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s64 = h.solve(X, tol=1e-8, workspace=ws)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        Xm = X0.clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sm, sf = sbec.solve_mixed(h, hm2, Xm, tol=1e-8, tol_mixed=1e-3, workspace=ws)
-        torch.cuda.synchronize()
-        tmx = time.perf_counter() - t0
-        hm2.close()
-        tts = {"fp64": {"seconds": t64, "energy": s64["energy"], "grad_norm": s64["grad_norm"],
-                        "outer": s64["outer_iters"], "inner": s64["inner_iters"], "rgbb": s64["rgbb_iters"],
-                        "n_grad": s64["n_grad"], "n_hvp": s64["n_hvp"], "n_energy": s64["n_energy"],
-                        "converged": bool(s64["converged"])},
-               "mixed_refined": {"seconds": tmx, "energy": sf["energy"], "grad_norm": sf["grad_norm"],
-                                 "mixed_phase": {k: sm[k] for k in ("outer_iters", "inner_iters", "rgbb_iters",
-                                                                    "n_hvp")},
-                                 "fp64_phase": {k: sf[k] for k in ("outer_iters", "inner_iters", "rgbb_iters",
-                                                                   "n_hvp")},
-                                 "converged": bool(sf["converged"])},
-               "speedup_mixed_over_fp64": t64 / tmx if tmx > 0 else None,
-               "energy_rel_diff": abs(sf["energy"] - s64["energy"]) / abs(s64["energy"])}
+    if not args.no_solve and args.workload != "spin3_3d_256":
+        tts = time_to_ground_state(args, sbec, torch, dev, stream, groups, w_main)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        ostep = oracle_step_runner(w)
-        ostep()
-        t0 = time.perf_counter()
-        n = 0
-        while time.perf_counter() - t0 < 15.0 and n < 50:
-            ostep()
-            n += 1
-        dt = time.perf_counter() - t0
+        n, dt = cpu_sample(w_main)
         cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} full steps of the {w.name} workload on one host thread"}
+               "sample": f"{n} full steps of the {w_main.name} workload on one host thread"
+                         + (" (one 256^2 instance of the batch)" if args.workload == "batch512" else "")}
 
-    h.close()
+    for h, _, _ in groups:
+        h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": w.name, "F": w.F, "grid": list(w.n), "components": w.C,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32 (FFT, pointwise) + f64 (reductions)",
+                "data": "synthetic",
+                "config": {"workload": wname, "F": w_main.F, "grid": list(w_main.n), "components": w_main.C,
+                           "instances": n_inst,
                            "step": "grad + riemannian hessvec + R1 retract + energy",
-                           "l2": f"inputs larger than L2: {NSTATES} resident states, "
-                                 f"{NSTATES * states[0].numel() * 16 / 1e6:.0f} MB",
+                           "l2": f"inputs larger than L2: {nstates} resident state(s) per size class, "
+                                 f"{sum(st[0].numel() * elem * len(st) for _, st, _ in groups) / 1e6:.0f} MB",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "status": status,
                 "mixed_fp32_value": mixed_value,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
-                "time_to_ground_state_s": tts["fp64"]["seconds"] if tts else None,
+                "time_to_ground_state_s": (tts or {}).get("fp64", {}).get("seconds"),
                 "time_to_ground_state": tts}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
+    tol = solve_tol(args.workload)
+    if args.workload == "batch512":
+        out = {"tol": tol, "classes": []}
+        t_all = 0.0
+        for h, _, ws in groups:
+            X = torch.from_numpy(np.stack([W.initial_fields(x) for x in ws])).to(dev).to(
+                torch.complex128 if args.precision == "fp64" else torch.complex64)
+            nb = 10 * X.numel() * X.element_size()
+            ws_buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = sbec.solve_batch(h, X, tol=tol, workspace=ws_buf)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            t_all += dt
+            out["classes"].append({"grid": list(ws[0].n), "instances": len(ws), "seconds": dt,
+                                   "converged": int(sum(s["converged"] for s in sts)),
+                                   "max_outer": int(max(s["outer_iters"] for s in sts)),
+                                   "max_inner": int(max(s["inner_iters"] for s in sts)),
+                                   "energies_head": [s["energy"] for s in sts[:3]]})
+        out["fp64" if args.precision == "fp64" else "mixed"] = {"seconds": t_all}
+        return out
+    h = groups[0][0]
+    X0 = torch.from_numpy(W.initial_fields(w)).to(dev)
+    if w.levels:
+        # cascadic multigrid, coarse levels to 1e-5 (Sec. 7.1)
+        lv = [w.at(n) for n in w.levels] + [w]
+        hf = h if args.precision == "fp64" else sbec.Handle.from_workload(w, stream=stream.cuda_stream)
+        hs = [sbec.Handle.from_workload(x, stream=stream.cuda_stream) for x in lv[:-1]] + [hf]
+        states = [torch.from_numpy(W.initial_fields(lv[0])).to(dev)] + [
+            torch.empty((x.C,) + x.shape, dtype=torch.complex128, device=dev) for x in lv[1:]]
+        ws = torch.empty(10 * states[-1].numel() * 16, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64 = sbec.solve_cascadic(hs, states, tol=tol, workspace=ws)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        for x in hs[:-1]:
+            x.close()
+        if hf is not h:
+            hf.close()
+        return {"tol": tol, "levels": [list(x.n) for x in lv],
+                "fp64": {"seconds": t64, "energy": s64["energy"], "grad_norm": s64["grad_norm"],
+                         "outer": s64["outer_iters"], "inner": s64["inner_iters"], "rgbb": s64["rgbb_iters"],
+                         "n_hvp": s64["n_hvp"], "converged": bool(s64["converged"])}}
+    nb64 = 10 * X0.numel() * 16
+    ws = torch.empty(nb64 + 11 * X0.numel() * 8, dtype=torch.uint8, device=dev)
+    hf = h if args.precision == "fp64" else sbec.Handle.from_workload(w, stream=stream.cuda_stream)
+    hm2 = sbec.Handle.from_workload(w, precision="mixed", stream=stream.cuda_stream)
+    X = X0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s64 = hf.solve(X, tol=tol, workspace=ws)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    Xm = X0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sm, sf = sbec.solve_mixed(hf, hm2, Xm, tol=tol, tol_mixed=1e-3, workspace=ws)
+    torch.cuda.synchronize()
+    tmx = time.perf_counter() - t0
+    hm2.close()
+    if hf is not h:
+        hf.close()
+    return {"tol": tol,
+            "fp64": {"seconds": t64, "energy": s64["energy"], "grad_norm": s64["grad_norm"],
+                     "outer": s64["outer_iters"], "inner": s64["inner_iters"], "rgbb": s64["rgbb_iters"],
+                     "n_grad": s64["n_grad"], "n_hvp": s64["n_hvp"], "n_energy": s64["n_energy"],
+                     "converged": bool(s64["converged"])},
+            "mixed_refined": {"seconds": tmx, "energy": sf["energy"], "grad_norm": sf["grad_norm"],
+                              "mixed_phase": {k: sm[k] for k in ("outer_iters", "inner_iters", "rgbb_iters",
+                                                                 "n_hvp")},
+                              "fp64_phase": {k: sf[k] for k in ("outer_iters", "inner_iters", "rgbb_iters",
+                                                                "n_hvp")},
+                              "converged": bool(sf["converged"])},
+            "speedup_mixed_over_fp64": t64 / tmx if tmx > 0 else None,
+            "energy_rel_diff": abs(sf["energy"] - s64["energy"]) / abs(s64["energy"])}
 
 
 def main():

@@ -106,7 +106,10 @@ __device__ __forceinline__ double block_sum_partials(const double* __restrict__ 
 // tw[m] = exp(-2 pi i m / n), m = 0..n-1; INV uses the conjugate twiddles and
 // the conjugate DFT (unnormalised both ways).
 // ---------------------------------------------------------------------------
-template <typename T2, bool INV, int ITEMS>
+// PFAST: consecutive threads take consecutive pencils (for tiles stored element-major,
+// buf[e * P + p], so that a warp's accesses are unit-stride); otherwise consecutive
+// threads take consecutive butterflies of one pencil (rows stored pencil-major).
+template <typename T2, bool INV, int ITEMS, bool PFAST = false>
 __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, int es,
                                             const T2* __restrict__ tw, int tid, int nth) {
     const int n = 1 << logn;
@@ -123,7 +126,8 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
             for (int it = 0; it < ITEMS; ++it) {
                 const int idx = tid + it * nth;
                 if (idx < total) {
-                    const int p = idx >> lognb, j = idx & (nb - 1);
+                    const int p = PFAST ? (idx & (P - 1)) : (idx >> lognb);
+                    const int j = PFAST ? (idx / P) : (idx & (nb - 1));
                     const T2* pb = buf + p * ps;
                     T2 a0 = pb[j * es], a1 = pb[(j + nb) * es], a2 = pb[(j + 2 * nb) * es],
                        a3 = pb[(j + 3 * nb) * es];
@@ -163,7 +167,8 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
         const int half = n >> 1;
         const int total = P * half;
         for (int idx = tid; idx < total; idx += nth) {
-            const int p = idx >> (logn - 1), j = idx & (half - 1);
+            const int p = PFAST ? (idx & (P - 1)) : (idx >> (logn - 1));
+            const int j = PFAST ? (idx / P) : (idx & (half - 1));
             T2* pb = buf + p * ps;
             const T2 a0 = pb[j * es];
             T2 a1 = pb[(j + half) * es];

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
         buf[idx] = src[base + e * a.estride + w];
     }
     __syncthreads();
-    fft_pencils<T2, MODE == S_INV, ITEMS>(buf, logn, W, 1, W, tw, tid, nth);
+    fft_pencils<T2, MODE == S_INV, ITEMS, true>(buf, logn, W, 1, W, tw, tid, nth);
 
     if (MODE == S_K2 || MODE == S_PARSEVAL) {
         double acc[1] = {0.0};
@@ -269,13 +269,74 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
             return;
         }
         __syncthreads();
-        fft_pencils<T2, true, ITEMS>(buf, logn, W, 1, W, tw, tid, nth);
+        fft_pencils<T2, true, ITEMS, true>(buf, logn, W, 1, W, tw, tid, nth);
     }
     T2* __restrict__ dst = reinterpret_cast<T2*>(a.out);
     for (int idx = tid; idx < W * n; idx += nth) {
         const int e = idx / W, w = idx - e * W;
         dst[base + e * a.estride + w] = buf[idx];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Stand-alone epilogues (used when the inverse x pass only transforms): the
+// gradient (Eq. 3.12) or Hessian-vector product (Eq. 3.13) of every grid point
+// from L X (or L Z) in `lx`, with the same partial sums as the fused x pass.
+// blockIdx.y is the instance; partials of instance b are blocks b*gridDim.x ...
+// ---------------------------------------------------------------------------
+template <typename T, int F, bool HESS>
+__global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp, long long G) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
+    const long long inst = blockIdx.y;
+    const long long foff = inst * (long long)C * G;
+    const T2* __restrict__ LX = reinterpret_cast<const T2*>(lxp) + foff;
+    const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X) + foff;
+    const T2* __restrict__ Zp = HESS ? reinterpret_cast<const T2*>(a.Zd) + foff : nullptr;
+    T2* __restrict__ dst = a.out ? reinterpret_cast<T2*>(a.out) + foff : nullptr;
+    const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * G;
+    const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
+    const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < G; pt += (long long)gridDim.x * blockDim.x) {
+        T2 x[C], l[C], o[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) { x[c] = Xp[c * G + pt]; l[c] = LX[c * G + pt]; }
+        const T V = Vp[pt];
+        Dens<F, T2> D;
+        D.compute(x);
+        if (!HESS) {
+            grad_point<F, T2>(x, D, V, pp, l, o);
+            double ek = 0.0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) ek += double(x[c].x * l[c].x + x[c].y * l[c].y);
+            acc[0] += 0.5 * ek + D.energy_density(x, double(V), pp);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                acc[1 + c] += double(cabs2(x[c]));
+                acc[1 + C + c] += double(x[c].x * o[c].x + x[c].y * o[c].y);
+                if (dst) dst[c * G + pt] = o[c];
+            }
+        } else {
+            T2 z[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) z[c] = Zp[c * G + pt];
+            hess_point<F, T2>(x, z, D, V, pp, l, o);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                T sh = T(a.sigslot >= 0 ? a.sigma * scal[a.sigslot] : a.sigma);
+                if (a.riem) sh -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
+                caxpy(o[c], sh, z[c]);
+                acc[c] += double(cabs2(x[c]));
+                acc[C + c] += double(x[c].x * o[c].x + x[c].y * o[c].y);
+                dst[c * G + pt] = o[c];
+            }
+        }
+    }
+    block_reduce_store<NQ>(acc, a.partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,6 +897,15 @@ static int elem_blocks(long long G, int num_sms, int B = 1) {
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+// The inverse x pass carries the nonlinear epilogue itself (one pass less over the
+// field) unless the handle computes in float: there the pass is bound by memory,
+// and the spin-2/3 epilogue's registers would cap it at one block per SM, so the
+// transform and the epilogue run as two kernels.
+template <typename T>
+static bool split_epilogue(const Geom& g) {
+    return sizeof(T) == 4 && g.dim > 1;
+}
+
 static PointParams point_params(const Geom& g) {
     PointParams pp;
     for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
@@ -983,6 +1053,18 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         if (st) return st;
         st = middle_passes<T>(g, w, s);
         if (st) return st;
+        if (split_epilogue<T>(g)) {
+            // inverse x-FFT in place, then the pointwise epilogue at full occupancy
+            st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
+            if (st) return st;
+            const int ne = elem_blocks(g.G, w.num_sms, g.B);
+            XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
+            a.X = X;
+            SBEC_LAUNCH(K_X_INV_GRAD, (k_epilogue<T, F, false>), dim3(ne, g.B), 256, a, w.work, g.G);
+            SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                        SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+            goto rgrad;
+        }
         XArgs a = xargs<T>(g, c, w.work, gout, w.partA);
         a.X = X;
         st = launch_x<T, F, X_INV_GRAD>(c, a, w, s);
@@ -990,6 +1072,7 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
     }
     SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
                 SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+rgrad:
     if (Griem || want_norm) {
         const int nb = elem_blocks(g.G, w.num_sms, g.B);
         SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
@@ -1059,6 +1142,19 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (st) return st;
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
+        if (split_epilogue<T>(g)) {
+            st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
+            if (st) return st;
+            const int ne = elem_blocks(g.G, w.num_sms, g.B);
+            SBEC_LAUNCH(K_X_INV_HESS, (k_epilogue<T, F, true>), dim3(ne, g.B), 256, a, w.work, g.G);
+            if (riem) {
+                SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
+                            S_PA, S_PB, 0);
+                SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
+                            w.partB);
+            }
+            return SBEC_OK;
+        }
         st = launch_x<T, F, X_INV_HESS>(c, a, w, s);
         if (st) return st;
     }
@@ -1233,7 +1329,7 @@ template <typename T>
 size_t Ops<T>::partials_needed(const Geom& g, int num_sms) {
     const XCfg c = xcfg<T>(g);
     size_t need = (size_t)c.nblk * (1 + 2 * g.C);
-    const size_t e = (size_t)elem_blocks(g.G, num_sms, g.B) * g.B * (2 * g.C);
+    const size_t e = (size_t)elem_blocks(g.G, num_sms, g.B) * g.B * (1 + 2 * g.C);
     if (e > need) need = e;
     for (int ax = 1; ax < g.dim; ++ax) {
         const SCfg sc = scfg<T>(g, ax, num_sms);
