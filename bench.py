@@ -256,6 +256,19 @@ def roofline_of(prof, w, precision, B, wname):
             "kernel": kname, "kernel_share": kms / total, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
 
 
+def aggregate(dist, elapsed_s, units_per_rank, device=None):
+    """Whole-job rate over replicas: the slowest rank's time bounds the job, so
+    value = units on all ranks / max over ranks of the elapsed time."""
+    import torch
+    world = dist.get_world_size() if dist is not None else 1
+    t = elapsed_s
+    if dist is not None:
+        x = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1907_01194_gb300 import sbec
@@ -274,11 +287,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not pg:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return aggregate(pg, x, 1.0, dev)[1]
 
     stream = torch.cuda.current_stream()
     cdt = torch.complex128 if args.precision == "fp64" else torch.complex64

@@ -109,9 +109,14 @@ __device__ __forceinline__ double block_sum_partials(const double* __restrict__ 
 // PFAST: consecutive threads take consecutive pencils (for tiles stored element-major,
 // buf[e * P + p], so that a warp's accesses are unit-stride); otherwise consecutive
 // threads take consecutive butterflies of one pencil (rows stored pencil-major).
-template <typename T2, bool INV, int ITEMS, bool PFAST = false>
+// PAD: logical slot i lives at i + i/8 (smem_slot), which spreads the stride-4
+// Stockham writes of pencil-major rows over all banks.
+__device__ __forceinline__ int smem_slot(int i) { return i + (i >> 3); }
+
+template <typename T2, bool INV, int ITEMS, bool PFAST = false, bool PAD = false>
 __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, int es,
                                             const T2* __restrict__ tw, int tid, int nth) {
+#define SLOT(i) (PAD ? smem_slot(i) : (i))
     const int n = 1 << logn;
     int Ns = 1;
     if (logn >= 2) {
@@ -128,9 +133,9 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
                 if (idx < total) {
                     const int p = PFAST ? (idx & (P - 1)) : (idx >> lognb);
                     const int j = PFAST ? (idx / P) : (idx & (nb - 1));
-                    const T2* pb = buf + p * ps;
-                    T2 a0 = pb[j * es], a1 = pb[(j + nb) * es], a2 = pb[(j + 2 * nb) * es],
-                       a3 = pb[(j + 3 * nb) * es];
+                    const int pb = p * ps;
+                    T2 a0 = buf[SLOT(pb + j * es)], a1 = buf[SLOT(pb + (j + nb) * es)],
+                       a2 = buf[SLOT(pb + (j + 2 * nb) * es)], a3 = buf[SLOT(pb + (j + 3 * nb) * es)];
                     const int k = j & (Ns - 1);
                     if (k != 0) {
                         T2 w1 = tw[k * twstep], w2 = tw[2 * k * twstep], w3 = tw[3 * k * twstep];
@@ -153,9 +158,8 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
             for (int it = 0; it < ITEMS; ++it) {
                 const int idx = tid + it * nth;
                 if (idx < total) {
-                    T2* pb = buf + dst[it];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) pb[r * Ns * es] = v[it][r];
+                    for (int r = 0; r < 4; ++r) buf[SLOT(dst[it] + r * Ns * es)] = v[it][r];
                 }
             }
             __syncthreads();
@@ -169,19 +173,20 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
         for (int idx = tid; idx < total; idx += nth) {
             const int p = PFAST ? (idx & (P - 1)) : (idx >> (logn - 1));
             const int j = PFAST ? (idx / P) : (idx & (half - 1));
-            T2* pb = buf + p * ps;
-            const T2 a0 = pb[j * es];
-            T2 a1 = pb[(j + half) * es];
+            const int i0 = SLOT(p * ps + j * es), i1 = SLOT(p * ps + (j + half) * es);
+            const T2 a0 = buf[i0];
+            T2 a1 = buf[i1];
             if (j != 0) {
                 T2 w = tw[j];
                 if (INV) w = cconj(w);
                 a1 = cmul(a1, w);
             }
-            pb[j * es] = cadd(a0, a1);
-            pb[(j + half) * es] = csub(a0, a1);
+            buf[i0] = cadd(a0, a1);
+            buf[i1] = csub(a0, a1);
         }
         __syncthreads();
     }
+#undef SLOT
 }
 
 // ---------------------------------------------------------------------------
