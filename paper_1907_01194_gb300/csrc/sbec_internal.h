@@ -17,6 +17,7 @@ enum {
     S_PB = 9,          // projection coefficient beta_w
     S_NORM2 = 10,      // scratch squared norm
     S_XFORM = 11,      // reserved
+    S_SKIP = 12,       // nonzero: every kernel leaves this instance of a batch untouched
     S_SIG = 16,        // 7 retraction scales sigma_l (component index order)
     S_SOLVER = 32,     // solver scalars start here
     S_COUNT = 128
@@ -46,6 +47,7 @@ struct Geom {
     int B;
     const void* ppb;          // PointParams[B]
     const double* Mb;         // M[B]
+    const double* skip;       // the handle's scalar blocks (S_SKIP flags of a batch)
 };
 
 // Kernel identities for the per-kernel launch counter and event timer.

@@ -20,6 +20,11 @@
 
 namespace sbec {
 
+// instance `inst` of a batch is switched off by its scalar block (S_SKIP)
+__device__ __forceinline__ bool skipped(const double* scal0, long long inst) {
+    return scal0 != nullptr && scal0[inst * S_COUNT + S_SKIP] != 0.0;
+}
+
 #define SBEC_CUDA_TRY(expr)                                   \
     do {                                                      \
         cudaError_t e_ = (expr);                              \
@@ -68,6 +73,7 @@ struct XArgs {
     PointParams pp;
     long long rpi;              // grid rows (x lines) per instance
     const PointParams* ppb;     // per-instance point parameters (batches) or null
+    const double* skip;         // scalar blocks (S_SKIP flags) or null
 };
 
 template <typename T, int F, int MODE, int ITEMS>
@@ -90,6 +96,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * a.G;
     const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
+    if (skipped(a.skip, inst)) return;
 
     for (int idx = tid; idx < P * n; idx += nth) {
         const int p = idx >> logn, e = idx & (n - 1);
@@ -224,6 +231,8 @@ struct SArgs {
     double invG;
     double* partials;
     int nblk;
+    int C;                // components (instance = pencil component / C)
+    const double* skip;   // scalar blocks (S_SKIP flags) or null
 };
 
 template <typename T, int MODE, int ITEMS>
@@ -237,6 +246,7 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
     const int xt = (int)(b % a.ntx); b /= a.ntx;
     const int o = (int)(b % a.nouter);
     const int c = (int)(b / a.nouter);
+    if (skipped(a.skip, c / a.C)) return;
     const long long obase = (a.axis == 1) ? (long long)o * a.ny * a.nx : (long long)o * a.nx;
     const long long base = (long long)c * a.G + obase + (long long)xt * W;
     const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in);
@@ -298,6 +308,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
     const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * G;
     const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
+    if (skipped(a.skip, inst)) return;
     double acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
@@ -348,9 +359,11 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
 
 // partials: n_l = |u_l|^2 (q = l index), t_l = <u_l, w_l> (q = C + l)
 template <typename T, int F>
-__global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials) {
+__global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials,
+                                                    const double* skip) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
+    if (skipped(skip, blockIdx.y)) return;
     const long long foff = (long long)blockIdx.y * C * G;
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
@@ -375,6 +388,7 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
                                                     double* partials) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
+    if (skipped(scal0, blockIdx.y)) return;
     const long long foff = (long long)blockIdx.y * C * G;
     const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
@@ -403,6 +417,7 @@ __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* X
                                                    double* partials, const double* __restrict__ scal0, int tslot) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
+    if (skipped(scal0, blockIdx.y)) return;
     const long long foff = (long long)blockIdx.y * C * G;
     if (tslot >= 0) t *= scal0[(size_t)blockIdx.y * S_COUNT + tslot];
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
@@ -429,6 +444,7 @@ template <typename T, int F>
 __global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal0) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
+    if (skipped(scal0, blockIdx.y)) return;
     const long long foff = (long long)blockIdx.y * C * G;
     const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
     T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
@@ -475,6 +491,7 @@ static __global__ void k_fin_energy(const double* pa, int na_tot, int na_inst, i
                                     int nb_inst, double* scal0) {
     __shared__ double va[4], vb[1];
     const int b = blockIdx.x;
+    if (skipped(scal0, b)) return;
     const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
     warp_sums(pa, na_tot, b * na_inst, na_inst, qa, nqa, va);
     if (pb) warp_sums(pb, nb_tot, b * nb_inst, nb_inst, qb, 1, vb);
@@ -495,6 +512,7 @@ static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int
                                   const double* Mb, double* scal0, int slot_a, int slot_b, int write_grad_info) {
     const int C = 2 * F + 1;
     const int b = blockIdx.x;
+    if (skipped(scal0, b)) return;
     __shared__ double v[15];
     int qs[15];
     int nq = 0;
@@ -529,6 +547,7 @@ static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int
 }
 
 static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, double* scal0, int slot) {
+    if (skipped(scal0, blockIdx.x)) return;
     __shared__ double v[1];
     const int q[1] = {0};
     warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, q, 1, v);
@@ -559,6 +578,7 @@ __device__ __forceinline__ double warp_sum_bcast(double v) {
 
 static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst, int F, double M0, const double* Mb,
                                        int kind, double* scal0) {
+    if (skipped(scal0, blockIdx.x)) return;
     __shared__ double m[7];
     const int C = 2 * F + 1;
     const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
@@ -670,6 +690,7 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
     // blockIdx.y is the instance, N the reals per instance
     const long long off = (long long)blockIdx.y * N;
     const double* scal = scal0 + (size_t)blockIdx.y * S_COUNT;
+    if (skipped(scal0, blockIdx.y)) return;
     const T* A = reinterpret_cast<const T*>(L.A) + off;
     const T* B = L.B ? reinterpret_cast<const T*>(L.B) + off : nullptr;
     const T* D1 = L.D1 ? reinterpret_cast<const T*>(L.D1) + off : nullptr;
@@ -700,7 +721,8 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
 // partials q0 = <A, B>, q1 = <C, D> (C null: skip)
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, const void* Cp, const void* Dp,
-                                              long long N, double* partials) {
+                                              long long N, double* partials, const double* skip) {
+    if (skipped(skip, blockIdx.y)) return;
     const long long off = (long long)blockIdx.y * N;
     const T* __restrict__ A = reinterpret_cast<const T*>(Ap) + off;
     const T* __restrict__ B = reinterpret_cast<const T*>(Bp) + off;
@@ -717,7 +739,8 @@ __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, co
 // partials q0 = <u - up, g - gp>, q1 = |g - gp|^2 (the BB quantities s^T v, v^T v)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp, const void* Gp, const void* GPp,
-                                                long long N, double* partials) {
+                                                long long N, double* partials, const double* skip) {
+    if (skipped(skip, blockIdx.y)) return;
     const long long off = (long long)blockIdx.y * N;
     const T* __restrict__ U = reinterpret_cast<const T*>(Up) + off;
     const T* __restrict__ UP = reinterpret_cast<const T*>(UPp) + off;
@@ -735,6 +758,7 @@ __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp,
 
 // scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2), per instance
 static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int nq, double* scal0, int slot) {
+    if (skipped(scal0, blockIdx.x)) return;
     __shared__ double v[2];
     const int qs[2] = {0, 1};
     warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, nq, v);
@@ -751,7 +775,7 @@ static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int
 // instance; scal[dst + 1] is the guard flag of the guarded updates
 static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
                                int mask) {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || skipped(scal0, blockIdx.x)) return;
     double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
     bool ok = (mask < 0) || (scal[mask] != 0.0);
     if (guard_kap >= 0) ok = ok && scal[guard_kap] > eps * scal[guard_pp];
@@ -999,6 +1023,8 @@ static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void*
     a.estride = (axis == 1) ? (long long)g.n[0] : (long long)g.n[0] * g.n[1];
     a.invG = g.invG;
     a.partials = part; a.nblk = c.nblk;
+    a.C = g.C;
+    a.skip = g.B > 1 ? g.skip : nullptr;
     return a;
 }
 
@@ -1012,6 +1038,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.pp = point_params(g);
     a.rpi = g.G / g.n[0];
     a.ppb = reinterpret_cast<const PointParams*>(g.ppb);
+    a.skip = g.B > 1 ? g.skip : nullptr;
     return a;
 }
 
@@ -1118,7 +1145,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
     const void* zin = Z;
     if (riem) {
         // xi = P_u Z (Lemma 4.1)
-        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.B), 256, X, Z, g.G, w.partB);
+        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.B), 256, X, Z, g.G, w.partB, w.scal);
         SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partB, nb * g.B, nb, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA, S_PB,
                     0);
         SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB,
@@ -1229,7 +1256,7 @@ int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, con
                  cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
     const int nb = elem_blocks(N / 2, w.num_sms, g.B);
-    SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.B), 256, A, B, C, D, N, w.partB);
+    SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.B), 256, A, B, C, D, N, w.partB, w.scal);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, C ? 2 : 1, w.scal, slot);
     return SBEC_OK;
 }
@@ -1239,7 +1266,7 @@ int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, 
                    int slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
     const int nb = elem_blocks(N / 2, w.num_sms, g.B);
-    SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.B), 256, U, UP, Gv, GP, N, w.partB);
+    SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.B), 256, U, UP, Gv, GP, N, w.partB, w.scal);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, slot);
     return SBEC_OK;
 }

@@ -347,6 +347,14 @@ struct BatchSolver {
         L.D1 = D1; L.D2 = D2; L.guard = guard;
         return Ops<T>::lincomb(g, w, L, slot, s);
     }
+    // only the instances with run[b] set take part in the next launches (the others'
+    // arrays and scalars stay as they are); takes effect with the next push()
+    void runset(const std::vector<char>& run) {
+        for (int b = 0; b < B; ++b) hs(b)[sbec::S_SKIP] = run[b] ? 0.0 : 1.0;
+    }
+    void runall() {
+        for (int b = 0; b < B; ++b) hs(b)[sbec::S_SKIP] = 0.0;
+    }
     int grad(const void* u, void* gE, void* rg) {
         for (int b = 0; b < B; ++b) ++st[b].n_grad;
         return Ops<T>::grad(g, w, u, gE, rg, true, s);
@@ -360,6 +368,8 @@ struct BatchSolver {
 
     int rgbb(void* u, void* up, void* z, void* rg, void* rgp, double tol, long long maxit, std::vector<double>& E,
              std::vector<double>& gn, std::vector<char>& act) {
+        runset(act);
+        TRY(push());
         TRY(energy(u));
         TRY(pull());
         std::vector<double> Ck(B), Qk(B, 1.0), t(B), slope(B), Ez(B);
@@ -377,6 +387,7 @@ struct BatchSolver {
                 any = any || act[b];
             }
             if (!any) return SBEC_OK;
+            runset(act);
             for (int b = 0; b < B; ++b) {
                 double gam = 1e-3;
                 if (have_prev) {
@@ -391,6 +402,7 @@ struct BatchSolver {
             }
             for (int bt = 0; bt <= 10; ++bt) {
                 for (int b = 0; b < B; ++b) hs(b)[SL_T] = act[b] ? -t[b] : 0.0;
+                runset(tr);                              // accepted trials are kept as they are
                 TRY(push());
                 TRY(Ops<T>::retract(g, w, u, rg, 1.0, o.retraction, z, s, SL_T));
                 TRY(energy(z));
@@ -409,6 +421,7 @@ struct BatchSolver {
                 if (act[b] && !isfinite(Ez[b])) act[b] = 0;       // no admissible trial: stop this instance
                 hs(b)[SL_ACT] = act[b] ? 1.0 : 0.0;
             }
+            runset(act);
             TRY(push());
             TRY(lin(up, 1.0, u, 0.0, nullptr, -1, SL_ACT));
             TRY(lin(rgp, 1.0, rg, 0.0, nullptr, -1, SL_ACT));
@@ -428,6 +441,8 @@ struct BatchSolver {
 
     int arnt(void* u, void* z, void* gE, void* rg, void* x, void* r, void* p, void* Hp, double tol, long long maxit,
              std::vector<double>& E, std::vector<double>& gn) {
+        runall();
+        TRY(push());
         TRY(energy(u));
         TRY(pull());
         for (int b = 0; b < B; ++b) E[b] = hs(b)[SBEC_S_ENERGY];
@@ -451,6 +466,8 @@ struct BatchSolver {
                 stop[b] = fmin(0.1, gn[b]) * gn[b];
                 hs(b)[SL_SIG] = sigma[b];
             }
+            runset(act);
+            TRY(push());
             // ---- modified CG, lock-step over the instances still in it ----
             TRY(lin(x, 0.0, rg, 0.0, nullptr));
             TRY(lin(r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
@@ -467,6 +484,7 @@ struct BatchSolver {
             while (incg) {
                 const int rr_now = parity ? SL_RRB : SL_RRA, rr_next = parity ? SL_RRA : SL_RRB;
                 for (int b = 0; b < B; ++b) { hs(b)[SL_CG] = cg[b] ? 1.0 : 0.0; hs(b)[SL_SIG] = sigma[b]; }
+                runset(cg);                              // finished CG runs keep p, Hp, x, r
                 TRY(push());
                 for (int b = 0; b < B; ++b) ++st[b].n_hvp;
                 TRY(Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, s, SL_SIG));
@@ -504,6 +522,7 @@ struct BatchSolver {
                 parity ^= 1;
             }
             // ---- xi (Eq. xi) into x ----
+            runset(act);
             bool anyneg = false, anyhd = false;
             for (int b = 0; b < B; ++b) {
                 hs(b)[SL_NEG] = (act[b] && neg[b]) ? 1.0 : 0.0;
@@ -542,6 +561,7 @@ struct BatchSolver {
             for (int b = 0; b < B; ++b) { t[b] = 1.0; ls[b] = act[b]; mz[b] = INFINITY; }
             for (int bt = 0; bt <= 10; ++bt) {
                 for (int b = 0; b < B; ++b) hs(b)[SL_T] = act[b] ? t[b] : 0.0;
+                runset(ls);                              // accepted trials are kept as they are
                 TRY(push());
                 TRY(Ops<T>::retract(g, w, u, x, 1.0, o.retraction, z, s, SL_T));
                 TRY(lin(r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));
@@ -562,6 +582,8 @@ struct BatchSolver {
                 }
                 if (!more) break;
             }
+            runset(act);
+            TRY(push());
             TRY(energy(z));
             TRY(pull());
             bool anyacc = false;
@@ -582,12 +604,16 @@ struct BatchSolver {
                 hs(b)[SL_ACC] = acc ? 1.0 : 0.0;
                 anyacc = anyacc || acc;
             }
+            std::vector<char> accv(B);
+            for (int b = 0; b < B; ++b) accv[b] = hs(b)[SL_ACC] != 0.0;
+            runset(accv);                                // rejected instances keep u, g, grad
             TRY(push());
             if (anyacc) {
                 TRY(lin(u, 1.0, z, 0.0, nullptr, -1, SL_ACC));
                 TRY(grad(u, gE, rg));
                 TRY(pull());
-                for (int b = 0; b < B; ++b) gn[b] = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]);
+                for (int b = 0; b < B; ++b)
+                    if (accv[b]) gn[b] = sqrt(hs(b)[SBEC_S_RGRAD_NORM2]);
             }
             for (int b = 0; b < B; ++b)
                 if (act[b] && sig_hat[b] > 1e20) act[b] = 0;
@@ -598,6 +624,9 @@ struct BatchSolver {
     int run(void* Xdev) {
         void *u = f[0], *up = f[1], *z = f[2], *gE = f[3], *rg = f[4], *rgp = f[5];
         if (cudaMemcpyAsync(u, Xdev, h->field_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return SBEC_ERR_CUDA;
+        TRY(pull());
+        runall();
+        TRY(push());
         if (o.project_initial) {
             TRY(Ops<T>::retract(g, w, u, u, 0.0, 1, u, s));
             TRY(pull());
@@ -614,6 +643,8 @@ struct BatchSolver {
             for (int b = 0; b < B; ++b) any = any || gn[b] > o.tol;
             if (any) TRY(arnt(u, z, gE, rg, f[6], f[7], f[8], f[9], o.tol, o.maxit, E, gn));
         }
+        runall();
+        TRY(push());
         TRY(grad(u, nullptr, rg));
         TRY(pull());
         bool all = true;
