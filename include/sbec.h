@@ -132,6 +132,13 @@ typedef struct sbec_solve_opts {
     double rgbb_tol;         /* warm-start tolerance inside ARNT (Sec. 7.1: 1e-2) */
     int    rgbb_maxit;       /* warm-start cap inside ARNT (Sec. 7.1: 2000) */
     int    project_initial;  /* 1: replace X by P_M(X) (Lemma 5.1) before iterating */
+    int    cg_chunk;         /* modified-CG iterations run between two host reads of the
+                                scalar block (>= 1; default 4).  The CG stopping tests run
+                                on the device; an instance whose CG has ended leaves the
+                                rest of its chunk untouched, so results do not depend on it */
+    int    cuda_graphs;      /* 1 (default): every CG chunk is the replay of a CUDA graph
+                                captured once per solve; 0: its kernels are launched one
+                                by one.  Graphs are not used while sbec_profile is on */
 } sbec_solve_opts;
 
 typedef struct sbec_stats {
@@ -145,7 +152,7 @@ typedef struct sbec_stats {
 } sbec_stats;
 
 /* Paper defaults: ARNT with R1, tol 1e-6, maxit 10000, RGBB warm start to 1e-2
- * or 2000 iterations, project_initial 1. */
+ * or 2000 iterations, project_initial 1; cg_chunk 4, cuda_graphs 1. */
 void sbec_solve_defaults(sbec_solve_opts* opts);
 
 /* Bytes of device workspace sbec_solve needs for the handle's problem (ten fields). */

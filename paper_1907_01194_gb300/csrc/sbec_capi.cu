@@ -263,8 +263,8 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
             ce = cudaMemcpyAsync(h->d_Mb, Mb, (size_t)B * sizeof(double), cudaMemcpyHostToDevice, h->stream);
         g.ppb = h->d_ppb;
         g.Mb = h->d_Mb;
-        g.skip = h->work.scal;
     }
+    g.skip = h->work.scal;
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
     free(hostbuf);
     if (ce != cudaSuccess) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }

@@ -47,7 +47,7 @@ struct Geom {
     int B;
     const void* ppb;          // PointParams[B]
     const double* Mb;         // M[B]
-    const double* skip;       // the handle's scalar blocks (S_SKIP flags of a batch)
+    const double* skip;       // the handle's scalar blocks: S_SKIP != 0 switches an instance off
 };
 
 // Kernel identities for the per-kernel launch counter and event timer.

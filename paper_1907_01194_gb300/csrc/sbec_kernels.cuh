@@ -1024,7 +1024,7 @@ static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void*
     a.invG = g.invG;
     a.partials = part; a.nblk = c.nblk;
     a.C = g.C;
-    a.skip = g.B > 1 ? g.skip : nullptr;
+    a.skip = g.skip;
     return a;
 }
 
@@ -1038,7 +1038,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.pp = point_params(g);
     a.rpi = g.G / g.n[0];
     a.ppb = reinterpret_cast<const PointParams*>(g.ppb);
-    a.skip = g.B > 1 ? g.skip : nullptr;
+    a.skip = g.skip;
     return a;
 }
 

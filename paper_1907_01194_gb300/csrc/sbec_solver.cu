@@ -2,8 +2,11 @@
 // kernels: RGBB (Riemannian gradient, BB step, Zhang-Hager nonmonotone search)
 // and ARNT (regularised Newton model m_k, modified CG, curvilinear Armijo
 // search, ratio test and sigma update).  Every vector operation runs on the
-// device; the host keeps the scalar control flow and reads a small block of
-// scalars once per CG iteration, line-search trial or outer iteration.
+// device.  The modified CG runs in chunks of cg_chunk iterations whose
+// coefficients and stopping tests are computed on the device (k_cg_ctl), each
+// chunk the replay of a CUDA graph; the host reads the scalar block once per
+// chunk, line-search trial or outer iteration and keeps the rest of the control
+// flow.
 //
 // Readings where the paper defers to the cited ARNT paper or is silent:
 //  * RGBB: first step gamma_0 = 1e-3; BB step |<s,v>|/<v,v> clamped to
@@ -45,6 +48,157 @@ enum {
     SL_RRB = SL_D0 + 8,           // <r, r> of odd iterations (pair)
     SL_MA = SL_D0 + 10,           // <dz, g>, <dz, dz>
     SL_MB = SL_D0 + 12,           // <dz, H dz>
+    SL_T = SL_D0 + 14,            // step length per instance
+    SL_SIG = SL_D0 + 15,          // sigma per instance
+    SL_ACT = SL_D0 + 16,          // instance still iterating
+    SL_CG = SL_D0 + 17,           // instance still in the modified CG
+    SL_BETA = SL_D0 + 18,         // CG beta
+    SL_TAU = SL_D0 + 19,          // tau of Eq. (xi)
+    SL_NEG = SL_D0 + 20,          // xi = -grad
+    SL_HD = SL_D0 + 21,           // xi = s + tau d
+    SL_ACC = SL_D0 + 22,          // trial accepted
+    SL_J = SL_D0 + 23,            // CG iterations run
+    SL_STOP = SL_D0 + 24,         // CG residual threshold min(0.1, ||grad||) ||grad||
+    SL_MAXIN = SL_D0 + 25,        // CG iteration cap
+    SL_SEST = SL_D0 + 26,         // |<p,Hp>| / <p,p> at a non-positive-curvature exit, else -1
+    SL_CGNEG = SL_D0 + 27,        // CG ended at its first iteration on curvature: xi = -grad
+    SL_CGHD = SL_D0 + 28,         // CG ended later on negative curvature: xi = s + tau d
+};
+static_assert(SL_CGHD < sbec::S_COUNT, "solver slots exceed the scalar block");
+
+// S_SKIP value of an instance whose modified CG has ended inside a chunk
+constexpr double kSkipCg = 2.0;
+
+// Modified-CG bookkeeping of one iteration, one thread per instance (after the
+// x and r updates): counts the iteration; ends the CG on non-positive curvature
+// <p,Hp> <= 1e-12 <p,p> (recording sigma_est and which direction Eq. (xi)
+// takes), on ||r|| <= the threshold or at the iteration cap; otherwise writes
+// beta = <r',r'>/<r,r> for the update p = r' + beta p.  An instance that ends
+// sets S_SKIP so that the rest of its chunk leaves its arrays and scalars alone.
+__global__ void k_cg_ctl(double* scal0, int B, int rr_now, int rr_next) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double* sc = scal0 + (size_t)b * sbec::S_COUNT;
+    if (sc[sbec::S_SKIP] != 0.0) return;
+    const double kap = sc[SL_KAP], pp = sc[SL_KAP + 1], rrn = sc[rr_next];
+    const double j = sc[SL_J] + 1.0;
+    sc[SL_J] = j;
+    bool done;
+    if (kap <= 1e-12 * pp) {
+        sc[SL_SEST] = fabs(kap) / pp;
+        if (j == 1.0) sc[SL_CGNEG] = 1.0;
+        else if (kap < -1e-12 * pp) sc[SL_CGHD] = 1.0;
+        done = true;
+    } else if (sqrt(rrn) <= sc[SL_STOP]) {
+        done = true;
+    } else {
+        sc[SL_BETA] = rrn / sc[rr_now];
+        done = j >= sc[SL_MAXIN];
+    }
+    if (done) {
+        sc[SL_CG] = 0.0;
+        sc[sbec::S_SKIP] = kSkipCg;
+    }
+}
+
+// S_SKIP of every instance back to 0
+__global__ void k_unskip(double* scal0, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) scal0[(size_t)b * sbec::S_COUNT + sbec::S_SKIP] = 0.0;
+}
+
+int clear_skip(sbec_handle* h) {
+    k_unskip<<<(h->B + 127) / 128, 128, 0, h->stream>>>(h->work.scal, h->B);
+    return cudaGetLastError() == cudaSuccess ? SBEC_OK : SBEC_ERR_CUDA;
+}
+
+// Chunks of the modified CG (Sec. 5, Eq. prob-lsub) on Hess m_k p = Hess f p +
+// sigma p with sigma from each instance's SL_SIG: per iteration the projected
+// Hessian-vector product, <p,Hp> and <p,p>, alpha = <r,r>/<p,Hp> (guarded),
+// x += alpha p, r -= alpha Hp with <r,r>, k_cg_ctl and p = r + beta p.  With
+// graphs, the chunk for a given state array and slot parity is captured once
+// on a private stream and replayed on the handle's stream.
+template <typename T>
+struct CgChunks {
+    sbec_handle* h;
+    const sbec::Geom& g;
+    const sbec::Work& w;
+    int K;
+    bool graphs;
+    cudaStream_t cap = nullptr;
+    struct Entry { const void* u; int par; cudaGraphExec_t exec; long long nodes; };
+    std::vector<Entry> cache;
+
+    CgChunks(sbec_handle* hh, int k, bool gr)
+        : h(hh), g(hh->geom), w(hh->work), K(k), graphs(gr && !(hh->work.prof && hh->work.prof->enabled)) {}
+    ~CgChunks() {
+        for (auto& e : cache) cudaGraphExecDestroy(e.exec);
+        if (cap) cudaStreamDestroy(cap);
+    }
+
+    int lin(cudaStream_t cs, void* out, const void* A, double cb, const void* Bv, int ib, int guard,
+            const void* D1, int slot) {
+        Lin L;
+        L.out = out; L.A = A; L.B = Bv; L.ca = 1.0; L.cb = cb; L.ia = -1; L.ib = ib; L.ineg = -1;
+        L.D1 = D1; L.D2 = nullptr; L.guard = guard;
+        return Ops<T>::lincomb(g, w, L, slot, cs);
+    }
+
+    int launch(cudaStream_t cs, const void* u, void* p, void* Hp, void* x, void* r, int par0) {
+        for (int i = 0; i < K; ++i) {
+            const int par = (par0 + i) & 1;
+            const int rr_now = par ? SL_RRB : SL_RRA, rr_next = par ? SL_RRA : SL_RRB;
+            int e = Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, cs, SL_SIG);
+            if (!e) e = Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, cs);
+            if (!e) e = Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, cs);
+            if (!e) e = lin(cs, x, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1, nullptr, SL_D0);
+            if (!e) e = lin(cs, r, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, rr_next);
+            if (e) return e;
+            {
+                sbec::ProfScope ps(w.prof, sbec::K_FIN, cs);
+                k_cg_ctl<<<(g.B + 127) / 128, 128, 0, cs>>>(w.scal, g.B, rr_now, rr_next);
+                if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
+            }
+            e = lin(cs, p, r, 1.0, p, SL_BETA, -1, nullptr, SL_D0);
+            if (e) return e;
+        }
+        return SBEC_OK;
+    }
+
+    // one chunk on the handle's stream, starting at slot parity par0
+    int run(const void* u, void* p, void* Hp, void* x, void* r, int par0) {
+        if (!graphs) return launch(h->stream, u, p, Hp, x, r, par0);
+        const Entry* hit = nullptr;
+        for (const auto& e : cache)
+            if (e.u == u && e.par == par0) hit = &e;
+        if (!hit) {
+            if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return SBEC_ERR_CUDA;
+            sbec::Prof* pr = w.prof;
+            const long long before = pr ? pr->launches : 0;
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                cudaGetLastError();
+                return SBEC_ERR_CUDA;
+            }
+            const int e = launch(cap, u, p, Hp, x, r, par0);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+            Entry ent{u, par0, nullptr, pr ? pr->launches - before : 0};
+            if (pr) pr->launches = before;       // captured, not launched
+            if (e || ce != cudaSuccess || !graph) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return e ? e : SBEC_ERR_CUDA;
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&ent.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) { cudaGetLastError(); return SBEC_ERR_CUDA; }
+            cache.push_back(ent);
+            hit = &cache.back();
+        }
+        if (cudaGraphLaunch(hit->exec, h->stream) != cudaSuccess) { cudaGetLastError(); return SBEC_ERR_CUDA; }
+        if (w.prof) w.prof->launches += hit->nodes;
+        return SBEC_OK;
+    }
 };
 
 constexpr double kEps = 2.220446049250313e-16;
@@ -59,9 +213,10 @@ struct Solver {
     sbec_stats* st;
     void* f[10];
     int status = SBEC_OK;
+    CgChunks<T> cgc;
 
     Solver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt)
-        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt) {
+        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), cgc(hh, oo.cg_chunk, oo.cuda_graphs != 0) {
         char* b = static_cast<char*>(ws);
         for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
     }
@@ -69,6 +224,13 @@ struct Solver {
     // scalars of the block after the launched work; returns the device status
     int pull() { return sbec_read_scalars(h); }
     double sc(int i) const { return h->h_scal[i]; }
+    // host-written slots back to the device (the block is in sync after pull)
+    int push() {
+        return cudaMemcpyAsync(w.scal, h->h_scal, sbec::S_COUNT * sizeof(double), cudaMemcpyHostToDevice, s) ==
+                       cudaSuccess
+                   ? SBEC_OK
+                   : SBEC_ERR_CUDA;
+    }
 
     int lin(void* out, double ca, const void* A, double cb, const void* B, int ib = -1, int guard = -1,
             const void* D1 = nullptr, const void* D2 = nullptr, int slot = SL_D0) {
@@ -168,26 +330,28 @@ struct Solver {
             bool s_is_neg_rg = false, have_d = false;
             double sig_est = -1.0;
             if (rr > 0.0) {
-                for (int j = 0; j < max_inner; ++j) {
-                    const int rr_now = (j & 1) ? SL_RRB : SL_RRA, rr_next = (j & 1) ? SL_RRA : SL_RRB;
-                    TRY(hess(u, p, sigma, 1, Hp));
-                    TRY(Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, s));
-                    TRY(Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s));
-                    TRY(lin(x, 1.0, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1));
-                    TRY(lin(r, 1.0, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, nullptr, rr_next));
+                // device-driven chunks (k_cg_ctl); the host reads the block once per chunk
+                double* hsc = h->h_scal;
+                hsc[SL_SIG] = sigma; hsc[SL_STOP] = stop; hsc[SL_MAXIN] = (double)max_inner;
+                hsc[SL_J] = 0.0; hsc[SL_CG] = 1.0; hsc[SL_SEST] = -1.0; hsc[SL_CGNEG] = 0.0; hsc[SL_CGHD] = 0.0;
+                hsc[sbec::S_SKIP] = 0.0;
+                TRY(push());
+                long long done_its = 0;
+                while (true) {
+                    TRY(cgc.run(u, p, Hp, x, r, (int)(done_its & 1)));
+                    done_its += cgc.K;
                     PULL(ds);
-                    ++st->inner_iters;
-                    const double kap = sc(SL_KAP), pp = sc(SL_KAP + 1), rrn = sc(rr_next);
-                    if (kap <= 1e-12 * pp) {
-                        sig_est = fabs(kap) / pp;
-                        if (j == 0) s_is_neg_rg = true;
-                        else if (kap < -1e-12 * pp) have_d = true;
-                        break;
-                    }
-                    if (sqrt(rrn) <= stop) break;
-                    TRY(lin(p, 1.0, r, rrn / rr, p));
-                    rr = rrn;
+                    if (sc(SL_CG) == 0.0) break;
+                            if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
                 }
+                const long long its = (long long)sc(SL_J);
+                st->inner_iters += its;
+                st->n_hvp += its;
+                if (sc(SL_CGNEG) != 0.0) s_is_neg_rg = true;
+                if (sc(SL_CGHD) != 0.0) have_d = true;
+                sig_est = sc(SL_SEST);
+                h->h_scal[sbec::S_SKIP] = 0.0;
+                TRY(push());
             }
             // ---- direction xi = s + tau d (Eq. xi), kept in x ----
             if (s_is_neg_rg) {
@@ -286,17 +450,6 @@ struct Solver {
 // instances are left unchanged (or recomputed identically).  The decisions are
 // those of Solver<T> applied to each instance.
 // ---------------------------------------------------------------------------
-enum {
-    SL_T = SL_D0 + 14,      // step length per instance
-    SL_SIG = SL_D0 + 15,    // sigma per instance
-    SL_ACT = SL_D0 + 16,    // instance still iterating
-    SL_CG = SL_D0 + 17,     // instance still in the modified CG
-    SL_BETA = SL_D0 + 18,   // CG beta
-    SL_TAU = SL_D0 + 19,    // tau of Eq. (xi)
-    SL_NEG = SL_D0 + 20,    // xi = -grad
-    SL_HD = SL_D0 + 21,     // xi = s + tau d
-    SL_ACC = SL_D0 + 22,    // trial accepted
-};
 
 template <typename T>
 struct BatchSolver {
@@ -309,9 +462,11 @@ struct BatchSolver {
     int B;
     void* f[10];
     std::vector<int> dstat;
+    CgChunks<T> cgc;
 
     BatchSolver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt)
-        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), B(hh->B), dstat(hh->B, 0) {
+        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), B(hh->B), dstat(hh->B, 0),
+          cgc(hh, oo.cg_chunk, oo.cuda_graphs != 0) {
         char* b = static_cast<char*>(ws);
         for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
     }
@@ -446,9 +601,9 @@ struct BatchSolver {
         TRY(energy(u));
         TRY(pull());
         for (int b = 0; b < B; ++b) E[b] = hs(b)[SBEC_S_ENERGY];
-        std::vector<double> sig_hat(B, 1.0), sig_floor(B, 0.0), sigma(B), rr(B), stop(B), sest(B), beta(B), t(B),
-            slope(B), mz(B), Ez(B);
-        std::vector<int> maxin(B), jj(B);
+        std::vector<double> sig_hat(B, 1.0), sig_floor(B, 0.0), sigma(B), rr(B), stop(B), sest(B), t(B), slope(B),
+            mz(B), Ez(B);
+        std::vector<int> maxin(B);
         std::vector<char> act(B), cg(B), neg(B), hd(B), ls(B);
         TRY(grad(u, gE, rg));
         TRY(pull());
@@ -474,52 +629,41 @@ struct BatchSolver {
             TRY(lin(p, 1.0, r, 0.0, nullptr));
             TRY(pull());
             bool incg = false;
+            int cap_in = 0;
             for (int b = 0; b < B; ++b) {
                 rr[b] = hs(b)[SL_RRA];
                 cg[b] = act[b] && rr[b] > 0.0;
-                jj[b] = 0; neg[b] = 0; hd[b] = 0; sest[b] = -1.0;
+                neg[b] = 0; hd[b] = 0; sest[b] = -1.0;
                 incg = incg || cg[b];
+                double* q = hs(b);
+                q[SL_CG] = cg[b] ? 1.0 : 0.0; q[SL_SIG] = sigma[b]; q[SL_STOP] = stop[b];
+                q[SL_MAXIN] = (double)maxin[b]; q[SL_J] = 0.0; q[SL_SEST] = -1.0; q[SL_CGNEG] = 0.0;
+                q[SL_CGHD] = 0.0;
+                if (cg[b] && maxin[b] > cap_in) cap_in = maxin[b];
             }
-            int parity = 0;
-            while (incg) {
-                const int rr_now = parity ? SL_RRB : SL_RRA, rr_next = parity ? SL_RRA : SL_RRB;
-                for (int b = 0; b < B; ++b) { hs(b)[SL_CG] = cg[b] ? 1.0 : 0.0; hs(b)[SL_SIG] = sigma[b]; }
-                runset(cg);                              // finished CG runs keep p, Hp, x, r
+            if (incg) {
+                runset(cg);                              // instances outside the CG keep p, Hp, x, r
                 TRY(push());
-                for (int b = 0; b < B; ++b) ++st[b].n_hvp;
-                TRY(Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, s, SL_SIG));
-                TRY(Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, s));
-                TRY(Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, s, SL_CG));
-                TRY(lin(x, 1.0, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1));
-                TRY(lin(r, 1.0, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, nullptr, rr_next));
-                TRY(pull());
-                incg = false;
+                // device-driven chunks (k_cg_ctl); the host reads the blocks once per chunk
+                long long done_its = 0;
+                while (true) {
+                    TRY(cgc.run(u, p, Hp, x, r, (int)(done_its & 1)));
+                    done_its += cgc.K;
+                    TRY(pull());
+                    bool more = false;
+                    for (int b = 0; b < B; ++b) more = more || (cg[b] && hs(b)[SL_CG] != 0.0);
+                    if (!more) break;
+                    if (done_its >= cap_in) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+                }
                 for (int b = 0; b < B; ++b) {
                     if (!cg[b]) continue;
-                    ++jj[b];
-                    ++st[b].inner_iters;
-                    const double kap = hs(b)[SL_KAP], pp = hs(b)[SL_KAP + 1], rrn = hs(b)[rr_next];
-                    if (kap <= 1e-12 * pp) {
-                        sest[b] = fabs(kap) / pp;
-                        if (jj[b] == 1) neg[b] = 1;
-                        else if (kap < -1e-12 * pp) hd[b] = 1;
-                        cg[b] = 0;
-                    } else if (sqrt(rrn) <= stop[b]) {
-                        cg[b] = 0;
-                    } else {
-                        beta[b] = rrn / rr[b];
-                        rr[b] = rrn;
-                        if (jj[b] >= maxin[b]) cg[b] = 0;
-                    }
-                    incg = incg || cg[b];
+                    const long long its = (long long)hs(b)[SL_J];
+                    st[b].inner_iters += its;
+                    st[b].n_hvp += its;
+                    neg[b] = hs(b)[SL_CGNEG] != 0.0;
+                    hd[b] = hs(b)[SL_CGHD] != 0.0;
+                    sest[b] = hs(b)[SL_SEST];
                 }
-                for (int b = 0; b < B; ++b) {
-                    hs(b)[SL_CG] = cg[b] ? 1.0 : 0.0;
-                    hs(b)[SL_BETA] = cg[b] ? beta[b] : 0.0;
-                }
-                TRY(push());
-                if (incg) TRY(lin(p, 1.0, r, 1.0, p, SL_BETA, SL_CG));
-                parity ^= 1;
             }
             // ---- xi (Eq. xi) into x ----
             runset(act);
@@ -661,6 +805,11 @@ struct BatchSolver {
 #undef TRY
 };
 
+bool opts_valid(const sbec_solve_opts& o) {
+    return o.retraction >= 1 && o.retraction <= 3 && o.tol > 0.0 && o.maxit >= 0 && o.rgbb_maxit >= 0 &&
+           o.cg_chunk >= 1 && o.cg_chunk <= 64 && (o.cuda_graphs == 0 || o.cuda_graphs == 1);
+}
+
 }  // namespace
 
 extern "C" {
@@ -674,6 +823,8 @@ void sbec_solve_defaults(sbec_solve_opts* o) {
     o->rgbb_tol = 1e-2;
     o->rgbb_maxit = 2000;
     o->project_initial = 1;
+    o->cg_chunk = 4;
+    o->cuda_graphs = 1;
 }
 
 int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
@@ -683,7 +834,7 @@ int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void*
         return SBEC_ERR_ARG;
     sbec_solve_opts o;
     if (opts) o = *opts; else sbec_solve_defaults(&o);
-    if (o.retraction < 1 || o.retraction > 3 || !(o.tol > 0.0) || o.maxit < 0 || o.rgbb_maxit < 0) return SBEC_ERR_ARG;
+    if (!opts_valid(o)) return SBEC_ERR_ARG;
     memset(stats, 0, sizeof(sbec_stats) * (size_t)h->B);
     int rc;
     if (h->prob.precision == SBEC_FP64) {
@@ -693,6 +844,7 @@ int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void*
         BatchSolver<float> S(h, o, workspace, stats);
         rc = S.run(X);
     }
+    if (clear_skip(h) && rc == SBEC_OK) rc = SBEC_ERR_CUDA;
     h->last_grad_X = nullptr;
     return rc;
 }
@@ -710,7 +862,7 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
     if (h->B != 1) return SBEC_ERR_ARG;       // batches: sbec_solve_batch
     sbec_solve_opts o;
     if (opts) o = *opts; else sbec_solve_defaults(&o);
-    if (o.retraction < 1 || o.retraction > 3 || !(o.tol > 0.0) || o.maxit < 0 || o.rgbb_maxit < 0) return SBEC_ERR_ARG;
+    if (!opts_valid(o)) return SBEC_ERR_ARG;
     sbec_stats local;
     sbec_stats* st = stats ? stats : &local;
     memset(st, 0, sizeof(*st));
@@ -730,6 +882,7 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
         Solver<float> S(h, o, workspace, st);
         rc = S.run(Xd);
     }
+    if (clear_skip(h) && rc == SBEC_OK) rc = SBEC_ERR_CUDA;
     h->last_grad_X = nullptr;
     if (host && (rc == SBEC_OK || rc == SBEC_ERR_NOCONV)) {
         if (cudaMemcpyAsync(X, Xd, h->field_bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
@@ -747,6 +900,7 @@ __global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, long lo
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = TD(src[i]);
 }
+
 }  // namespace
 
 extern "C" {

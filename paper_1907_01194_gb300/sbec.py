@@ -288,7 +288,7 @@ def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("retraction", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("rgbb_tol", ctypes.c_double), ("rgbb_maxit", ctypes.c_int),
-                ("project_initial", ctypes.c_int)]
+                ("project_initial", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -308,15 +308,26 @@ _lib.sbec_solve.restype = _int
 ARNT, RGBB = 0, 1
 
 
-def _solve(self, X, method="arnt", retraction=1, tol=1e-8, maxit=10000, rgbb_tol=1e-2,
-           rgbb_maxit=2000, project=True, workspace=None):
-    """Ground state from X (overwritten) by sbec_solve; returns the stats as a dict.
-    Raises SbecError unless the tolerance was reached (status NOCONV included)."""
+def _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project=True, cg_chunk=None, graphs=None):
+    """sbec_solve_opts from the library defaults and the given overrides (None keeps the
+    default: 4 CG iterations per chunk, CUDA graphs on)."""
     o = SolveOpts()
     _lib.sbec_solve_defaults(ctypes.byref(o))
     o.method = ARNT if method == "arnt" else RGBB
     o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
     o.rgbb_tol, o.rgbb_maxit, o.project_initial = float(rgbb_tol), int(rgbb_maxit), int(bool(project))
+    if cg_chunk is not None:
+        o.cg_chunk = int(cg_chunk)
+    if graphs is not None:
+        o.cuda_graphs = int(bool(graphs))
+    return o
+
+
+def _solve(self, X, method="arnt", retraction=1, tol=1e-8, maxit=10000, rgbb_tol=1e-2,
+           rgbb_maxit=2000, project=True, workspace=None, cg_chunk=None, graphs=None):
+    """Ground state from X (overwritten) by sbec_solve; returns the stats as a dict.
+    Raises SbecError unless the tolerance was reached (status NOCONV included)."""
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project, cg_chunk, graphs)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_workspace_bytes(self._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
     if workspace is None:
@@ -342,14 +353,10 @@ _lib.sbec_solve_mixed.restype = _int
 
 
 def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction=1, maxit=10000,
-                rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None):
+                rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None, graphs=None):
     """Mixed-precision solve on h32 then FP64 refinement on h64 (sbec_solve_mixed).
     X: complex128 device tensor, overwritten.  Returns (stats_mixed, stats_fp64)."""
-    o = SolveOpts()
-    _lib.sbec_solve_defaults(ctypes.byref(o))
-    o.method = ARNT if method == "arnt" else RGBB
-    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
-    o.rgbb_tol, o.rgbb_maxit = float(rgbb_tol), int(rgbb_maxit)
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_mixed_workspace_bytes(h64._h, h32._h, ctypes.byref(nb)),
            "sbec_solve_mixed_workspace_bytes")
@@ -380,14 +387,10 @@ def prolongate(hc, Xc, hf, Xf):
 
 
 def solve_cascadic(handles, states, tol=1e-8, tol_coarse=1e-5, method="arnt", retraction=1, maxit=10000,
-                   rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None):
+                   rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None, graphs=None):
     """sbec_solve_cascadic over handles (coarse to fine); states[j] is level j's array
     (states[0] holds the initial data, the finest receives the ground state)."""
-    o = SolveOpts()
-    _lib.sbec_solve_defaults(ctypes.byref(o))
-    o.method = ARNT if method == "arnt" else RGBB
-    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
-    o.rgbb_tol, o.rgbb_maxit = float(rgbb_tol), int(rgbb_maxit)
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_workspace_bytes(handles[-1]._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
     if workspace is None:
@@ -410,14 +413,10 @@ _lib.sbec_solve_batch.restype = _int
 
 
 def solve_batch(h, X, tol=1e-8, method="arnt", retraction=1, maxit=10000, rgbb_tol=1e-2, rgbb_maxit=2000,
-                project=True, workspace=None):
+                project=True, workspace=None, cg_chunk=None, graphs=None):
     """Lock-step ground-state solve of every instance of a batch handle (sbec_solve_batch).
     X: device tensor (B, C, ...), overwritten.  Returns a list of per-instance stats dicts."""
-    o = SolveOpts()
-    _lib.sbec_solve_defaults(ctypes.byref(o))
-    o.method = ARNT if method == "arnt" else RGBB
-    o.retraction, o.tol, o.maxit = int(retraction), float(tol), int(maxit)
-    o.rgbb_tol, o.rgbb_maxit, o.project_initial = float(rgbb_tol), int(rgbb_maxit), int(bool(project))
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project, cg_chunk, graphs)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_workspace_bytes(h._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
     if workspace is None:

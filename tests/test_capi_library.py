@@ -40,3 +40,19 @@ def test_binding_loads_and_resolves(lib):
     assert set(sbec.library_symbols()) == set(sbec.EXPORTED)
     assert sbec._lib.sbec_status_string(sbec.ERR_DOMAIN).decode().startswith("point outside")
 
+
+
+def test_solve_defaults_and_option_layout(lib):
+    # sbec_solve_defaults is host-only: the paper's solver settings plus the CG
+    # chunking defaults; the binding's struct matches the header's field order
+    import ctypes
+    from paper_1907_01194_gb300 import sbec
+    o = sbec.SolveOpts()
+    sbec._lib.sbec_solve_defaults(ctypes.byref(o))
+    assert (o.method, o.retraction, o.tol, o.maxit) == (sbec.ARNT, 1, 1e-6, 10000)
+    assert (o.rgbb_tol, o.rgbb_maxit, o.project_initial) == (1e-2, 2000, 1)
+    assert (o.cg_chunk, o.cuda_graphs) == (4, 1)
+    hdr = open(os.path.join(ROOT, "include", "sbec.h")).read()
+    body = hdr[hdr.index("typedef struct sbec_solve_opts"):hdr.index("} sbec_solve_opts;")]
+    fields = re.findall(r"^\s*(?:int|double)\s+(\w+);", body, re.M)
+    assert fields == [f for f, _ in sbec.SolveOpts._fields_]
