@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-ground-state solves")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     return ap.parse_args()
 
 
@@ -322,6 +323,8 @@ def run_ours(args, world, rank, local):
         n_inst = 1
     for h, st, _ in groups:
         h.sync()
+    # launch shapes: measured by the library's autotuner on each handle (not timed)
+    tiles = [h.get_tune() if args.no_autotune else h.autotune(st[0]) for h, st, _ in groups]
     bufs = [tuple(torch.empty_like(st[0]) for _ in range(3)) for _, st, _ in groups]
 
     def step(k):
@@ -413,6 +416,8 @@ def run_ours(args, world, rank, local):
     if args.precision == "fp64" and args.workload != "batch512":
         hm = sbec.Handle.from_workload(w_main, precision="mixed", stream=stream.cuda_stream)
         mst = [x.to(torch.complex64) for x in groups[0][1]]
+        if not args.no_autotune:
+            hm.autotune(mst[0])
         mb = tuple(torch.empty_like(mst[0]) for _ in range(3))
         save = groups[:], bufs[:]
         groups[:] = [(hm, mst, [w_main])]
@@ -454,7 +459,9 @@ def run_ours(args, world, rank, local):
                            "step": "grad + riemannian hessvec + R1 retract + energy",
                            "l2": f"inputs larger than L2: {nstates} resident state(s) per size class, "
                                  f"{sum(st[0].numel() * elem * len(st) for _, st, _ in groups) / 1e6:.0f} MB",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "tiles": {"autotuned": not args.no_autotune,
+                                     "shapes": [{k: v for k, v in t.items() if k != "ms"} for t in tiles]}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "status": status,
                 "mixed_fp32_value": mixed_value,
@@ -469,6 +476,13 @@ def run_ours(args, world, rank, local):
 
 def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
     tol = solve_tol(args.workload)
+
+    def tuned(hh, wl):
+        # launch shapes of a new handle by the autotuner, from the workload's initial data
+        if not args.no_autotune:
+            cdt = torch.complex128 if hh.precision == "fp64" else torch.complex64
+            hh.autotune(torch.from_numpy(W.initial_fields(wl)).to(dev).to(cdt))
+        return hh
     if args.workload == "batch512":
         out = {"tol": tol, "classes": []}
         t_all = 0.0
@@ -495,8 +509,8 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
     if w.levels:
         # cascadic multigrid, coarse levels to 1e-5 (Sec. 7.1)
         lv = [w.at(n) for n in w.levels] + [w]
-        hf = h if args.precision == "fp64" else sbec.Handle.from_workload(w, stream=stream.cuda_stream)
-        hs = [sbec.Handle.from_workload(x, stream=stream.cuda_stream) for x in lv[:-1]] + [hf]
+        hf = h if args.precision == "fp64" else tuned(sbec.Handle.from_workload(w, stream=stream.cuda_stream), w)
+        hs = [tuned(sbec.Handle.from_workload(x, stream=stream.cuda_stream), x) for x in lv[:-1]] + [hf]
         states = [torch.from_numpy(W.initial_fields(lv[0])).to(dev)] + [
             torch.empty((x.C,) + x.shape, dtype=torch.complex128, device=dev) for x in lv[1:]]
         ws = torch.empty(10 * states[-1].numel() * 16, dtype=torch.uint8, device=dev)
@@ -515,8 +529,8 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
                          "n_hvp": s64["n_hvp"], "converged": bool(s64["converged"])}}
     nb64 = 10 * X0.numel() * 16
     ws = torch.empty(nb64 + 11 * X0.numel() * 8, dtype=torch.uint8, device=dev)
-    hf = h if args.precision == "fp64" else sbec.Handle.from_workload(w, stream=stream.cuda_stream)
-    hm2 = sbec.Handle.from_workload(w, precision="mixed", stream=stream.cuda_stream)
+    hf = h if args.precision == "fp64" else tuned(sbec.Handle.from_workload(w, stream=stream.cuda_stream), w)
+    hm2 = tuned(sbec.Handle.from_workload(w, precision="mixed", stream=stream.cuda_stream), w)
     X = X0.clone()
     torch.cuda.synchronize()
     t0 = time.perf_counter()

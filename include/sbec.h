@@ -203,6 +203,41 @@ int sbec_sync(sbec_handle* h);
 /* Device pointer to the handle's scalar block (doubles, see SBEC_S_* slots). */
 const double* sbec_scalars(const sbec_handle* h);
 
+/* Launch shapes of the hot-path kernels (not in the paper: the paper's own
+ * kernels are MATLAB's).  x_rows: grid rows (x lines, all C components) per
+ * block of the x-axis FFT pass, a power of 2 dividing the rows of an
+ * instance.  s_pencils[a], a = 1, 2: pencils (consecutive x columns) per
+ * shared-memory tile of the FFT pass along axis a, a power of 2 <= n[0];
+ * s_split[a]: butterflies per thread of that pass (1, 2, 4 or 8).
+ * elem_per_sm: blocks per SM of the grid-stride elementwise and reduction
+ * kernels (1..32).  At most 16384 points per FFT block and 227 KB of shared
+ * memory.  [0] entries and the entries of axes >= dim are 0.  In
+ * sbec_set_tune a 0 field keeps the built-in choice. */
+typedef struct sbec_tune {
+    int    x_rows;
+    int    s_pencils[3];
+    int    s_split[3];
+    int    elem_per_sm;
+    double ms;     /* sbec_autotune: measured ms of one energy+gradient evaluation
+                      plus one Riemannian Hessian-vector product; otherwise 0 */
+} sbec_tune;
+
+/* Autotuner: times one energy+gradient evaluation plus one Riemannian
+ * Hessian-vector product at X (a device state of the handle, e.g. the initial
+ * data; its values only need to be finite) with CUDA events on the handle's
+ * stream, for each candidate of one field at a time (coordinate descent in the
+ * order of the struct, starting from the built-in choices), keeps a candidate
+ * that is more than 2% faster, and leaves the handle on the best shapes, which
+ * it also writes to *out.  reps: timed repetitions per candidate (0: enough
+ * for about 3 ms).  Uses the handle's staging arrays; synchronises the stream.
+ * Results do not depend on the shapes beyond the order of the partial sums. */
+int sbec_autotune(sbec_handle* h, const void* X, int reps, sbec_tune* out);
+/* Set shapes (e.g. an earlier sbec_autotune result): SBEC_ERR_ARG if invalid
+ * for the handle's problem.  sbec_get_tune: the shapes in use, the built-in
+ * choices filled in. */
+int sbec_set_tune(sbec_handle* h, const sbec_tune* t);
+int sbec_get_tune(const sbec_handle* h, sbec_tune* out);
+
 /* Launch bookkeeping (not in the paper: instrumentation of this library).
  * sbec_launch_count: number of library kernels launched on the handle so far.
  * sbec_profile(h, 1) starts recording a CUDA event pair around every kernel

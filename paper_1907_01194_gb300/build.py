@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsbec.so")
 
-SOURCES = ["sbec_capi.cu", "sbec_kernels_f64.cu", "sbec_kernels_f32.cu", "sbec_noalloc.cu", "sbec_solver.cu"]
+SOURCES = ["sbec_capi.cu", "sbec_kernels_f64.cu", "sbec_kernels_f32.cu", "sbec_noalloc.cu", "sbec_solver.cu",
+           "sbec_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]

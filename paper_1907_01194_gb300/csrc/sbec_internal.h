@@ -30,6 +30,15 @@ struct PointParams {
     double e0, e1, e2, e3;  // beta_i / (2 dV) (energy prefactors)
 };
 
+// Launch shapes of the passes (0 = the built-in choice); set by the autotuner
+// (sbec_autotune) or sbec_set_tune, checked by Ops<T>::tune_ok before use.
+struct Tune {
+    int x_rows;        // grid rows per block of the x pass
+    int s_pencils[3];  // pencils per tile of the strided pass along axis 1, 2 ([0] unused)
+    int s_split[3];    // butterfly items per thread of the strided pass (1, 2, 4, 8)
+    int elem_per_sm;   // blocks per SM (whole GPU, all instances) of the grid-stride kernels
+};
+
 // Geometry and parameters of one problem as the kernels see it.
 struct Geom {
     int F, C, dim;
@@ -48,6 +57,7 @@ struct Geom {
     const void* ppb;          // PointParams[B]
     const double* Mb;         // M[B]
     const double* skip;       // the handle's scalar blocks: S_SKIP != 0 switches an instance off
+    Tune tune;
 };
 
 // Kernel identities for the per-kernel launch counter and event timer.
@@ -128,7 +138,13 @@ template <typename T> struct Ops {
     static int init_tables(Geom& g, void* tw_storage, cudaStream_t s);
     static int harmonic_potential(const Geom& g, void* V, const double* lo, const double* hi, cudaStream_t s);
     static int convert_potential(const Geom& g, void* V, const double* Vd, cudaStream_t s);
-    static size_t partials_needed(const Geom& g, int num_sms);
+    // partial-sum slots for the shapes of g.tune, or (any_shape) for every
+    // shape tune_ok accepts
+    static size_t partials_needed(const Geom& g, int num_sms, bool any_shape = true);
+    // t is a valid set of launch shapes for g (0 fields: built-in choice)
+    static bool tune_ok(const Geom& g, const Tune& t);
+    // the launch shapes g resolves to (built-in choices filled in)
+    static Tune resolved(const Geom& g, int num_sms);
 };
 
 }  // namespace sbec

@@ -861,14 +861,28 @@ __global__ void k_convert(void* Vp, const double* Vd, long long G) {
 struct XCfg { int rpb, nth, items, nblk, nblk_inst; size_t smem; };
 struct SCfg { int W, nth, items, nblk, nblk_inst; size_t smem; };
 
+// Limits of the launch shapes: at most 4096 butterflies per block (512 threads x 8
+// items) and the opt-in dynamic shared memory of one block.
+constexpr int kMaxPointsPerBlock = 16384;
+constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int kMaxElemPerSm = 32;
+
+template <typename T>
+static size_t xsmem(int P, int n) {
+    return (size_t)(P * n + ((P * n) >> 3) + 1) * sizeof(typename C2<T>::t);   // padded slots (smem_slot)
+}
+
 // x pass: one block = rpb grid rows (x lines) of all C components of one instance
 template <typename T>
 static XCfg xcfg(const Geom& g) {
-    using T2 = typename C2<T>::t;
     const int n = g.n[0];
     const long long rows_inst = g.G / n;
     int rpb = 1;
-    while ((long long)rpb * 2 * g.C * n <= 2048 && rows_inst % (rpb * 2) == 0) rpb *= 2;
+    if (g.tune.x_rows > 0) {
+        rpb = g.tune.x_rows;
+    } else {
+        while ((long long)rpb * 2 * g.C * n <= 2048 && rows_inst % (rpb * 2) == 0) rpb *= 2;
+    }
     const int P = rpb * g.C;
     const int bfly = (n >= 4) ? P * n / 4 : P;
     int nth = ((bfly + 31) / 32) * 32;
@@ -881,7 +895,7 @@ static XCfg xcfg(const Geom& g) {
     c.rpb = rpb; c.nth = nth; c.items = it2;
     c.nblk_inst = (int)(rows_inst / rpb);
     c.nblk = c.nblk_inst * g.B;
-    c.smem = (size_t)(P * n + ((P * n) >> 3) + 1) * sizeof(T2);   // padded slots (smem_slot)
+    c.smem = xsmem<T>(P, n);
     return c;
 }
 
@@ -893,11 +907,16 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
     const int nx = g.n[0];
     const long long outer = (axis == 1) ? g.n[2] : g.n[1];
     int W = (sizeof(T) == 8) ? 8 : 16;
-    if (W > nx) W = nx;
-    // prefer at least 4 blocks per SM when the grid is small
-    while (W > 2 && (long long)g.B * g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
+    if (g.tune.s_pencils[axis] > 0) {
+        W = g.tune.s_pencils[axis];
+    } else {
+        if (W > nx) W = nx;
+        // prefer at least 4 blocks per SM when the grid is small
+        while (W > 2 && (long long)g.B * g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
+    }
     const int bfly = (n >= 4) ? W * n / 4 : W;
-    int nth = ((bfly + 31) / 32) * 32;
+    const int split = g.tune.s_split[axis] > 0 ? g.tune.s_split[axis] : 1;
+    int nth = ((bfly / split + 31) / 32) * 32;
     if (nth > 512) nth = 512;
     if (nth < 64) nth = 64;
     int items = (bfly + nth - 1) / nth;
@@ -912,9 +931,9 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
 }
 
 // blocks per instance of the grid-stride elementwise kernels
-static int elem_blocks(long long G, int num_sms, int B = 1) {
+static int elem_blocks(long long G, int num_sms, int B = 1, int per_sm = 0) {
     long long b = (G + 255) / 256;
-    long long cap = 8LL * num_sms / (B > 0 ? B : 1);
+    long long cap = (long long)(per_sm > 0 ? per_sm : 8) * num_sms / (B > 0 ? B : 1);
     if (cap < 1) cap = 1;
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
@@ -1083,7 +1102,7 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
             // inverse x-FFT in place, then the pointwise epilogue at full occupancy
             st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
             if (st) return st;
-            const int ne = elem_blocks(g.G, w.num_sms, g.B);
+            const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
             XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
             a.X = X;
             SBEC_LAUNCH(K_X_INV_GRAD, (k_epilogue<T, F, false>), dim3(ne, g.B), 256, a, w.work, g.G);
@@ -1100,7 +1119,7 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
                 SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
 rgrad:
     if (Griem || want_norm) {
-        const int nb = elem_blocks(g.G, w.num_sms, g.B);
+        const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
         SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
                     SBEC_S_BETA_G, w.partB);
         SBEC_LAUNCH(K_FIN, k_fin_norm, g.B, 256, w.partB, nb * g.B, nb, w.scal, SBEC_S_RGRAD_NORM2);
@@ -1141,7 +1160,7 @@ template <typename T, int F>
 static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
                   cudaStream_t s, int sigslot = -1) {
     constexpr int C = 2 * F + 1;
-    const int nb = elem_blocks(g.G, w.num_sms, g.B);
+    const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
     const void* zin = Z;
     if (riem) {
         // xi = P_u Z (Lemma 4.1)
@@ -1171,7 +1190,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (split_epilogue<T>(g)) {
             st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
             if (st) return st;
-            const int ne = elem_blocks(g.G, w.num_sms, g.B);
+            const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
             SBEC_LAUNCH(K_X_INV_HESS, (k_epilogue<T, F, true>), dim3(ne, g.B), 256, a, w.work, g.G);
             if (riem) {
                 SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
@@ -1195,7 +1214,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
 template <typename T, int F>
 static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
                      cudaStream_t s, int tslot = -1) {
-    const int nb = elem_blocks(g.G, w.num_sms, g.B);
+    const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
     SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.B), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot);
     SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.B, 256, w.partB, nb * g.B, nb, F, g.M, g.Mb, kind, w.scal);
     SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.B), 256, out, g.G, w.scal);
@@ -1244,7 +1263,7 @@ int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi,
 template <typename T>
 int Ops<T>::lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
     const bool dots = (L.D1 || L.D2);
     SBEC_LAUNCH(K_LIN, k_lincomb<T>, dim3(nb, g.B), 256, L, N, w.scal, dots ? w.partB : nullptr);
     if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, dot_slot);
@@ -1255,7 +1274,7 @@ template <typename T>
 int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, const void* C, const void* D, int slot,
                  cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
     SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.B), 256, A, B, C, D, N, w.partB, w.scal);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, C ? 2 : 1, w.scal, slot);
     return SBEC_OK;
@@ -1265,7 +1284,7 @@ template <typename T>
 int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
                    int slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B);
+    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
     SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.B), 256, U, UP, Gv, GP, N, w.partB, w.scal);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, slot);
     return SBEC_OK;
@@ -1352,16 +1371,60 @@ int Ops<T>::convert_potential(const Geom& g, void* V, const double* Vd, cudaStre
 }
 
 template <typename T>
-size_t Ops<T>::partials_needed(const Geom& g, int num_sms) {
-    const XCfg c = xcfg<T>(g);
+size_t Ops<T>::partials_needed(const Geom& g, int num_sms, bool any_shape) {
+    // any_shape: the most blocks an accepted shape launches (one grid row per
+    // x-pass block, one pencil per strided tile, kMaxElemPerSm blocks per SM)
+    Geom h = g;
+    if (any_shape) {
+        h.tune = Tune{};
+        h.tune.x_rows = 1;
+        h.tune.elem_per_sm = kMaxElemPerSm;
+        for (int ax = 1; ax < g.dim; ++ax) h.tune.s_pencils[ax] = 1;
+    }
+    const XCfg c = xcfg<T>(h);
     size_t need = (size_t)c.nblk * (1 + 2 * g.C);
-    const size_t e = (size_t)elem_blocks(g.G, num_sms, g.B) * g.B * (1 + 2 * g.C);
+    const size_t e = (size_t)elem_blocks(g.G, num_sms, g.B, h.tune.elem_per_sm) * g.B * (1 + 2 * g.C);
     if (e > need) need = e;
     for (int ax = 1; ax < g.dim; ++ax) {
-        const SCfg sc = scfg<T>(g, ax, num_sms);
+        const SCfg sc = scfg<T>(h, ax, num_sms);
         if ((size_t)sc.nblk > need) need = sc.nblk;
     }
     return need;
+}
+
+template <typename T>
+bool Ops<T>::tune_ok(const Geom& g, const Tune& t) {
+    auto pow2 = [](int v) { return v >= 1 && (v & (v - 1)) == 0; };
+    if (t.x_rows != 0) {
+        const long long rows_inst = g.G / g.n[0];
+        if (!pow2(t.x_rows) || rows_inst % t.x_rows != 0) return false;
+        const long long pts = (long long)t.x_rows * g.C * g.n[0];
+        if (pts > kMaxPointsPerBlock || xsmem<T>(t.x_rows * g.C, g.n[0]) > kMaxSmem) return false;
+    }
+    if (t.s_pencils[0] != 0 || t.s_split[0] != 0) return false;
+    for (int ax = 1; ax < 3; ++ax) {
+        const int W = t.s_pencils[ax], sp = t.s_split[ax];
+        if (ax >= g.dim && (W != 0 || sp != 0)) return false;
+        if (sp != 0 && sp != 1 && sp != 2 && sp != 4 && sp != 8) return false;
+        if (W == 0) continue;
+        if (!pow2(W) || W > g.n[0]) return false;
+        const long long pts = (long long)W * g.n[ax];
+        if (pts > kMaxPointsPerBlock || (size_t)pts * sizeof(typename C2<T>::t) > kMaxSmem) return false;
+    }
+    if (t.elem_per_sm < 0 || t.elem_per_sm > kMaxElemPerSm) return false;
+    return true;
+}
+
+template <typename T>
+Tune Ops<T>::resolved(const Geom& g, int num_sms) {
+    Tune t{};
+    t.x_rows = xcfg<T>(g).rpb;
+    for (int ax = 1; ax < g.dim; ++ax) {
+        t.s_pencils[ax] = scfg<T>(g, ax, num_sms).W;
+        t.s_split[ax] = g.tune.s_split[ax] > 0 ? g.tune.s_split[ax] : 1;
+    }
+    t.elem_per_sm = g.tune.elem_per_sm > 0 ? g.tune.elem_per_sm : 8;
+    return t;
 }
 
 }  // namespace sbec

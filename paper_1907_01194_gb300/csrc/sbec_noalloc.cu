@@ -111,7 +111,7 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
     // carve the fixed array: twiddles, lambda^2, potential (when V is NULL), the
     // transformed field, two partial-sum areas and the scalar block
     const size_t ntw = (size_t)P.n[0] + P.n[1] + P.n[2];
-    const size_t part = sbec::Ops<double>::partials_needed(g, sms > 0 ? sms : 1);
+    const size_t part = sbec::Ops<double>::partials_needed(g, sms > 0 ? sms : 1, false);
     size_t off = 0;
     const size_t o_tw = off;   off += up256(2 * ntw);
     const size_t o_lam = off;  off += up256(ntw);

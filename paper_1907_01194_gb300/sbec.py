@@ -251,6 +251,56 @@ class Handle:
         return out
 
 
+class Tune(ctypes.Structure):
+    _fields_ = [("x_rows", ctypes.c_int), ("s_pencils", ctypes.c_int * 3), ("s_split", ctypes.c_int * 3),
+                ("elem_per_sm", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+_lib.sbec_autotune.argtypes = [_vp, _vp, _int, ctypes.POINTER(Tune)]
+_lib.sbec_autotune.restype = _int
+_lib.sbec_set_tune.argtypes = [_vp, ctypes.POINTER(Tune)]
+_lib.sbec_set_tune.restype = _int
+_lib.sbec_get_tune.argtypes = [_vp, ctypes.POINTER(Tune)]
+_lib.sbec_get_tune.restype = _int
+
+
+def _tune_dict(t):
+    return {"x_rows": t.x_rows, "s_pencils": list(t.s_pencils), "s_split": list(t.s_split),
+            "elem_per_sm": t.elem_per_sm, "ms": t.ms}
+
+
+def _autotune(self, X, reps=0):
+    """sbec_autotune at state X (device array): picks the launch shapes by timing,
+    leaves the handle on them and returns them as a dict (with the measured ms)."""
+    t = Tune()
+    _check(_lib.sbec_autotune(self._h, _ptr(X), int(reps), ctypes.byref(t)), "sbec_autotune")
+    return _tune_dict(t)
+
+
+def _get_tune(self):
+    """Launch shapes in use (sbec_get_tune)."""
+    t = Tune()
+    _check(_lib.sbec_get_tune(self._h, ctypes.byref(t)), "sbec_get_tune")
+    return _tune_dict(t)
+
+
+def _set_tune(self, d):
+    """Set launch shapes from a dict like autotune()'s (missing keys: built-in choice)."""
+    t = Tune()
+    t.x_rows = int(d.get("x_rows", 0))
+    for a, v in enumerate(d.get("s_pencils", [0, 0, 0])):
+        t.s_pencils[a] = int(v)
+    for a, v in enumerate(d.get("s_split", [0, 0, 0])):
+        t.s_split[a] = int(v)
+    t.elem_per_sm = int(d.get("elem_per_sm", 0))
+    _check(_lib.sbec_set_tune(self._h, ctypes.byref(t)), "sbec_set_tune")
+
+
+Handle.autotune = _autotune
+Handle.get_tune = _get_tune
+Handle.set_tune = _set_tune
+
+
 def library_symbols():
     """Names of the exported entry points that resolve in the loaded library."""
     return [name for name in EXPORTED if hasattr(_lib, name)]

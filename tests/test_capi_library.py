@@ -56,3 +56,11 @@ def test_solve_defaults_and_option_layout(lib):
     body = hdr[hdr.index("typedef struct sbec_solve_opts"):hdr.index("} sbec_solve_opts;")]
     fields = re.findall(r"^\s*(?:int|double)\s+(\w+);", body, re.M)
     assert fields == [f for f, _ in sbec.SolveOpts._fields_]
+
+
+def test_tune_struct_layout(lib):
+    from paper_1907_01194_gb300 import sbec
+    hdr = open(os.path.join(ROOT, "include", "sbec.h")).read()
+    body = hdr[hdr.index("typedef struct sbec_tune"):hdr.index("} sbec_tune;")]
+    fields = re.findall(r"^\s*(?:int|double)\s+(\w+)", body, re.M)
+    assert fields == [f for f, _ in sbec.Tune._fields_]
