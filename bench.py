@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-ground-state solves")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--tiles", default=None,
+                    help="launch shapes as JSON (keys of sbec_tune) instead of autotuning, e.g. for profiling")
     return ap.parse_args()
 
 
@@ -324,7 +326,12 @@ def run_ours(args, world, rank, local):
     for h, st, _ in groups:
         h.sync()
     # launch shapes: measured by the library's autotuner on each handle (not timed)
-    tiles = [h.get_tune() if args.no_autotune else h.autotune(st[0]) for h, st, _ in groups]
+    if args.tiles:
+        for h, _, _ in groups:
+            h.set_tune(json.loads(args.tiles))
+        tiles = [h.get_tune() for h, _, _ in groups]
+    else:
+        tiles = [h.get_tune() if args.no_autotune else h.autotune(st[0]) for h, st, _ in groups]
     bufs = [tuple(torch.empty_like(st[0]) for _ in range(3)) for _, st, _ in groups]
 
     def step(k):
@@ -460,7 +467,7 @@ def run_ours(args, world, rank, local):
                            "l2": f"inputs larger than L2: {nstates} resident state(s) per size class, "
                                  f"{sum(st[0].numel() * elem * len(st) for _, st, _ in groups) / 1e6:.0f} MB",
                            "parallelism": "replicas" if world > 1 else "single",
-                           "tiles": {"autotuned": not args.no_autotune,
+                           "tiles": {"autotuned": not (args.no_autotune or args.tiles),
                                      "shapes": [{k: v for k, v in t.items() if k != "ms"} for t in tiles]}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "status": status,

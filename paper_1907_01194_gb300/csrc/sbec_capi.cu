@@ -219,7 +219,8 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
 
     bool ok = true;
     ok = ok && cudaMalloc(&h->d_tw, ntw * h->elem) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&h->d_lam2, ntw * sizeof(double)) == cudaSuccess;
+    // lambda^2 (double) followed by lambda^2 / G in the handle's precision
+    ok = ok && cudaMalloc((void**)&h->d_lam2, ntw * (sizeof(double) + real_bytes)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->d_V, (size_t)B * g.G * real_bytes) == cudaSuccess;
     ok = ok && cudaMalloc(&h->work.work, h->field_bytes) == cudaSuccess;
     ok = ok && cudaMalloc(&h->work.work2, h->field_bytes) == cudaSuccess;
@@ -236,8 +237,9 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
 
     // lambda_p^2 = (2 pi p / (b - a))^2 with p the signed DFT frequency (Eq. 3.6);
     // per-instance parameters of a batch
-    const size_t host_bytes = ntw * sizeof(double) +
-                              (B > 1 ? (size_t)B * (sizeof(sbec::PointParams) + sizeof(double)) : 0);
+    const size_t tab_bytes = ntw * (sizeof(double) + real_bytes);
+    const size_t par_off = (tab_bytes + 15) & ~size_t(15);      // batch parameters, 16-byte aligned
+    const size_t host_bytes = par_off + (B > 1 ? (size_t)B * (sizeof(sbec::PointParams) + sizeof(double)) : 0);
     char* hostbuf = (char*)malloc(host_bytes);
     if (!hostbuf) { free_handle(h); return SBEC_ERR_CUDA; }
     double* lam = (double*)hostbuf;
@@ -253,9 +255,21 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
         g.lam2[ax] = h->d_lam2 + off;
         off += n;
     }
-    cudaError_t ce = cudaMemcpyAsync(h->d_lam2, lam, ntw * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    // |k|^2 / G tables of the pass precision: the FP32 passes scale and sum the
+    // kinetic term with FP32 arithmetic only
+    char* k2s = hostbuf + ntw * sizeof(double);
+    char* d_k2s = reinterpret_cast<char*>(h->d_lam2 + ntw);
+    for (int ax = 0, o = 0; ax < 3; ++ax) {
+        g.k2s[ax] = d_k2s + (size_t)o * real_bytes;
+        for (int j = 0; j < P.n[ax]; ++j, ++o) {
+            const double v = lam[o] * g.invG;
+            if (dbl) reinterpret_cast<double*>(k2s)[o] = v;
+            else reinterpret_cast<float*>(k2s)[o] = (float)v;
+        }
+    }
+    cudaError_t ce = cudaMemcpyAsync(h->d_lam2, lam, tab_bytes, cudaMemcpyHostToDevice, h->stream);
     if (B > 1 && ce == cudaSuccess) {
-        sbec::PointParams* ppb = (sbec::PointParams*)(hostbuf + ntw * sizeof(double));
+        sbec::PointParams* ppb = (sbec::PointParams*)(hostbuf + par_off);
         double* Mb = (double*)(ppb + B);
         for (int b = 0; b < B; ++b) { params(probs[b], ppb[b]); Mb[b] = probs[b].M; }
         ce = cudaMemcpyAsync(h->d_ppb, ppb, (size_t)B * sizeof(sbec::PointParams), cudaMemcpyHostToDevice, h->stream);

@@ -38,6 +38,37 @@ template <typename T2> __device__ __forceinline__ void cfma(T2& a, T2 b, T2 c) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-thread running sums of the reductions.  FP64 form: a double.  Mixed form:
+// a float sum whose rounding error is carried in a second float (the error-free
+// transformation TwoSum of Moller and Knuth, then cascaded as in Neumaier's
+// compensated summation), so that the FP32 kernels keep about twice float
+// precision in their partials without FP64 arithmetic per point (on this GPU the
+// FP64 pipe runs at 1/64 of the FP32 rate, below what HBM bandwidth needs).
+// value() hands the partial to the FP64 block reduction.
+// ---------------------------------------------------------------------------
+template <typename T> struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        const float bv = t - s;
+        c += (s - (t - bv)) + (v - bv);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+template <int NQ, typename T>
+__device__ __forceinline__ void acc_values(const Acc<T> (&a)[NQ], double (&v)[NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = a[q].value();
+}
+
+// ---------------------------------------------------------------------------
 // Deterministic reductions.  Each block reduces NQ doubles in a fixed order
 // (warp shuffles, then warp 0 over the per-warp results) and writes them to
 // partials[q * nblk + blk]; reduce_partials sums those in a fixed order too,
@@ -247,6 +278,18 @@ __device__ __forceinline__ constexpr double qnt_entry(int k, int i) {
 __device__ __forceinline__ constexpr int qnt_l(int k) { return 2 - k; }
 
 
+// PointParams in the arithmetic type of the pointwise code (converted once per
+// thread, so that the FP32 kernels do no FP64 arithmetic per point).
+template <typename T> struct PPT {
+    T bz[7], g0, g1, g2, g3, e0, e1, e2, e3;
+    __device__ __forceinline__ explicit PPT(const PointParams& p) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) bz[i] = T(p.bz[i]);
+        g0 = T(p.g0); g1 = T(p.g1); g2 = T(p.g2); g3 = T(p.g3);
+        e0 = T(p.e0); e1 = T(p.e1); e2 = T(p.e2); e3 = T(p.e3);
+    }
+};
+
 // Densities at one grid point (Sec. 3): rho, F_z, F_+, A00, A_{2l}.
 template <int F, typename T2>
 struct Dens {
@@ -291,19 +334,18 @@ struct Dens {
         }
     }
 
-    // interaction + potential + Zeeman energy density (kinetic part excluded)
-    __device__ __forceinline__ double energy_density(const T2 (&x)[2 * F + 1], double V,
-                                                     const PointParams& pp) const {
+    // interaction + potential + Zeeman energy density (kinetic part excluded), in T
+    __device__ __forceinline__ T energy_density(const T2 (&x)[2 * F + 1], T V, const PPT<T>& pp) const {
         constexpr int C = 2 * F + 1;
-        double e = V * double(rho);
+        T e = V * rho;
 #pragma unroll
-        for (int i = 0; i < C; ++i) e += pp.bz[i] * double(cabs2(x[i]));
-        double inter = pp.e0 * double(rho) * double(rho) + pp.e1 * (double(Fz) * double(Fz) + double(cabs2(Fp)));
-        if (F >= 2) inter += pp.e2 * double(cabs2(A00));
+        for (int i = 0; i < C; ++i) e += pp.bz[i] * cabs2(x[i]);
+        T inter = pp.e0 * rho * rho + pp.e1 * (Fz * Fz + cabs2(Fp));
+        if (F >= 2) inter += pp.e2 * cabs2(A00);
         if (F == 3) {
-            double q = 0;
+            T q = 0;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) q += double(cabs2(A2[k]));
+            for (int k = 0; k < 5; ++k) q += cabs2(A2[k]);
             inter += pp.e3 * q;
         }
         return e + inter;
@@ -313,7 +355,7 @@ struct Dens {
 // Gradient (Eq. 3.12) at one grid point, component k, given the Laplacian term lx_k.
 template <int F, typename T2>
 __device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<F, T2>& D, decltype(T2::x) V,
-                                           const PointParams& pp, const T2 (&lx)[2 * F + 1],
+                                           const PPT<decltype(T2::x)>& pp, const T2 (&lx)[2 * F + 1],
                                            T2 (&g)[2 * F + 1]) {
     using T = decltype(T2::x);
     constexpr int C = 2 * F + 1;
@@ -347,8 +389,9 @@ __device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<
 // Hessian-vector product (Eq. 3.13) at one grid point, given lz_k = (L Z)_k.
 template <int F, typename T2>
 __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&z)[2 * F + 1],
-                                           const Dens<F, T2>& D, decltype(T2::x) V, const PointParams& pp,
-                                           const T2 (&lz)[2 * F + 1], T2 (&hz)[2 * F + 1]) {
+                                           const Dens<F, T2>& D, decltype(T2::x) V,
+                                           const PPT<decltype(T2::x)>& pp, const T2 (&lz)[2 * F + 1],
+                                           T2 (&hz)[2 * F + 1]) {
     using T = decltype(T2::x);
     constexpr int C = 2 * F + 1;
     const T g0 = T(pp.g0), g1 = T(pp.g1), g2 = T(pp.g2), g3 = T(pp.g3);

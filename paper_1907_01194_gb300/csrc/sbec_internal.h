@@ -48,6 +48,7 @@ struct Geom {
     // device tables
     const void* tw[3];        // twiddles per axis, T2 (precision of the handle)
     const double* lam2[3];    // lambda_p^2 per axis in DFT index order
+    const void* k2s[3];       // lambda_p^2 / G per axis, T (precision of the handle)
     const void* V;            // potential, T
     double bz[7];
     double g0, g1, g2, g3, e0, e1, e2, e3;

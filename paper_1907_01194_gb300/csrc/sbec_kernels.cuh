@@ -60,6 +60,7 @@ struct XArgs {
     const void* V;
     const void* tw;
     const double* lam2x;
+    const void* k2x;      // T: lambda_p^2 / G along x (the precision of the pass)
     long long G;
     int logn;             // x length
     int rpb;              // row groups per block
@@ -75,6 +76,19 @@ struct XArgs {
     const PointParams* ppb;     // per-instance point parameters (batches) or null
     const double* skip;         // scalar blocks (S_SKIP flags) or null
 };
+
+// Shift of the Hessian epilogue per component: sigma (times the instance's
+// scal[sigslot] when sigslot >= 0), minus alpha_g + beta_g l in the Riemannian
+// form (Lemma 4.2), in the pass precision.
+template <int F, typename T>
+__device__ __forceinline__ void hess_shift(const XArgs& a, const double* scal, T (&shift)[2 * F + 1]) {
+#pragma unroll
+    for (int c = 0; c < 2 * F + 1; ++c) {
+        T s = T(a.sigslot >= 0 ? a.sigma * scal[a.sigslot] : a.sigma);
+        if (a.riem) s -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
+        shift[c] = s;
+    }
+}
 
 template <typename T, int F, int MODE, int ITEMS>
 __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
@@ -94,8 +108,9 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + foff;
     const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
     const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * a.G;
-    const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
+    const PPT<T> pp(a.ppb ? a.ppb[inst] : a.pp);
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
+    const T* __restrict__ k2x = reinterpret_cast<const T*>(a.k2x);
     if (skipped(a.skip, inst)) return;
 
     for (int idx = tid; idx < P * n; idx += nth) {
@@ -105,9 +120,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     }
     __syncthreads();
 
-    double acc[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    Acc<T> acc[NQ];
 
     if (MODE == X_FWD_EPW || MODE == X_FULL_ENERGY) {
         for (int idx = tid; idx < RPB * n; idx += nth) {
@@ -117,7 +130,7 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             for (int c = 0; c < C; ++c) x[c] = buf[smem_slot((rg * C + c) * n + e)];
             Dens<F, T2> D;
             D.compute(x);
-            acc[0] += D.energy_density(x, double(Vp[(row0 + rg) * n + e]), pp);
+            acc[0].add(D.energy_density(x, Vp[(row0 + rg) * n + e], pp));
         }
         __syncthreads();
     }
@@ -130,13 +143,14 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         // kinetic part by Parseval: (1/(2G)) sum |k|^2 |X^|^2
         for (int idx = tid; idx < P * n; idx += nth) {
             const int e = idx & (n - 1);
-            acc[1] += 0.5 * a.invG * a.lam2x[e] * double(cabs2(buf[smem_slot(idx)]));
+            if constexpr (sizeof(T) == 8) acc[1].add(0.5 * a.invG * a.lam2x[e] * cabs2(buf[smem_slot(idx)]));
+            else acc[1].add(T(0.5) * k2x[e] * cabs2(buf[smem_slot(idx)]));
         }
     }
     if (MODE == X_FULL_GRAD || MODE == X_FULL_HESS) {
         for (int idx = tid; idx < P * n; idx += nth) {
             const int e = idx & (n - 1);
-            buf[smem_slot(idx)] = cscale(buf[smem_slot(idx)], T(a.lam2x[e] * a.invG));
+            buf[smem_slot(idx)] = cscale(buf[smem_slot(idx)], k2x[e]);
         }
         __syncthreads();
     }
@@ -169,14 +183,14 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             Dens<F, T2> D;
             D.compute(x);
             grad_point<F, T2>(x, D, V, pp, lx, g);
-            double ek = 0.0;
+            T ek = 0;
 #pragma unroll
-            for (int c = 0; c < C; ++c) ek += double(x[c].x * lx[c].x + x[c].y * lx[c].y);
-            acc[0] += 0.5 * ek + D.energy_density(x, double(V), pp);
+            for (int c = 0; c < C; ++c) ek += x[c].x * lx[c].x + x[c].y * lx[c].y;
+            acc[0].add(T(0.5) * ek + D.energy_density(x, V, pp));
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                acc[1 + c] += double(cabs2(x[c]));
-                acc[1 + C + c] += double(x[c].x * g[c].x + x[c].y * g[c].y);
+                acc[1 + c].add(cabs2(x[c]));
+                acc[1 + C + c].add(x[c].x * g[c].x + x[c].y * g[c].y);
                 if (dst) dst[(long long)c * a.G + pt] = g[c];
             }
         }
@@ -186,6 +200,8 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X) + foff;
         const T2* __restrict__ Zp = reinterpret_cast<const T2*>(a.Zd) + foff;
         T2* __restrict__ dst = reinterpret_cast<T2*>(a.out) + foff;
+        T shift[C];
+        hess_shift<F, T>(a, scal, shift);
         for (int idx = tid; idx < RPB * n; idx += nth) {
             const int rg = idx >> logn, e = idx & (n - 1);
             const long long pt = (row0 + rg) * n + e;
@@ -202,17 +218,19 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
             hess_point<F, T2>(x, z, D, V, pp, lz, h);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                T s = T(a.sigslot >= 0 ? a.sigma * scal[a.sigslot] : a.sigma);
-                if (a.riem) s -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
-                caxpy(h[c], s, z[c]);
-                acc[c] += double(cabs2(x[c]));
-                acc[C + c] += double(x[c].x * h[c].x + x[c].y * h[c].y);
+                caxpy(h[c], shift[c], z[c]);
+                acc[c].add(cabs2(x[c]));
+                acc[C + c].add(x[c].x * h[c].x + x[c].y * h[c].y);
                 dst[(long long)c * a.G + pt] = h[c];
             }
         }
     }
 
-    if (MODE != X_FWD && MODE != X_INV) block_reduce_store<NQ>(acc, a.partials, a.nblk, blockIdx.x);
+    if (MODE != X_FWD && MODE != X_INV) {
+        double v[NQ];
+        acc_values(acc, v);
+        block_reduce_store<NQ>(v, a.partials, a.nblk, blockIdx.x);
+    }
 }
 
 struct SArgs {
@@ -220,6 +238,7 @@ struct SArgs {
     void* out;
     const void* tw;
     const double* lam2[3];
+    const void* k2t[3];   // T: lambda_p^2 / G per axis (the precision of the pass)
     long long G;
     int axis;         // 1 = y, 2 = z
     int logn;         // axis length
@@ -260,22 +279,31 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
     fft_pencils<T2, MODE == S_INV, ITEMS, true>(buf, logn, W, 1, W, tw, tid, nth);
 
     if (MODE == S_K2 || MODE == S_PARSEVAL) {
-        double acc[1] = {0.0};
+        Acc<T> acc[1];
+        const T* __restrict__ k0 = reinterpret_cast<const T*>(a.k2t[0]);
+        const T* __restrict__ k1 = reinterpret_cast<const T*>(a.k2t[1]);
+        const T* __restrict__ k2t = reinterpret_cast<const T*>(a.k2t[2]);
         for (int idx = tid; idx < W * n; idx += nth) {
             const int e = idx / W, w = idx - e * W;
             // frequency indices: x and the pass axis from the tile, the third axis from o
             const int ix = xt * W + w;
             const int iy = (a.axis == 1) ? e : o;
             const int iz = (a.axis == 2) ? e : o;
-            const double k2 = a.lam2[0][ix] + a.lam2[1][iy] + a.lam2[2][iz];
-            if (MODE == S_K2) {
-                buf[idx] = cscale(buf[idx], T(k2 * a.invG));
+            if constexpr (sizeof(T) == 8) {
+                const double k2 = a.lam2[0][ix] + a.lam2[1][iy] + a.lam2[2][iz];
+                if (MODE == S_K2) buf[idx] = cscale(buf[idx], T(k2 * a.invG));
+                else acc[0].add(0.5 * a.invG * k2 * cabs2(buf[idx]));
             } else {
-                acc[0] += 0.5 * a.invG * k2 * double(cabs2(buf[idx]));
+                // FP32: |k|^2 / G from the per-axis tables, no FP64 arithmetic per point
+                const T f = k0[ix] + k1[iy] + k2t[iz];
+                if (MODE == S_K2) buf[idx] = cscale(buf[idx], f);
+                else acc[0].add(T(0.5) * f * cabs2(buf[idx]));
             }
         }
         if (MODE == S_PARSEVAL) {
-            block_reduce_store<1>(acc, a.partials, a.nblk, blockIdx.x);
+            double v[1];
+            acc_values(acc, v);
+            block_reduce_store<1>(v, a.partials, a.nblk, blockIdx.x);
             return;
         }
         __syncthreads();
@@ -306,12 +334,12 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
     const T2* __restrict__ Zp = HESS ? reinterpret_cast<const T2*>(a.Zd) + foff : nullptr;
     T2* __restrict__ dst = a.out ? reinterpret_cast<T2*>(a.out) + foff : nullptr;
     const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * G;
-    const PointParams& pp = a.ppb ? a.ppb[inst] : a.pp;
+    const PPT<T> pp(a.ppb ? a.ppb[inst] : a.pp);
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
     if (skipped(a.skip, inst)) return;
-    double acc[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    T shift[C];
+    if (HESS) hess_shift<F, T>(a, scal, shift);
+    Acc<T> acc[NQ];
     for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < G; pt += (long long)gridDim.x * blockDim.x) {
         T2 x[C], l[C], o[C];
 #pragma unroll
@@ -321,14 +349,14 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
         D.compute(x);
         if (!HESS) {
             grad_point<F, T2>(x, D, V, pp, l, o);
-            double ek = 0.0;
+            T ek = 0;
 #pragma unroll
-            for (int c = 0; c < C; ++c) ek += double(x[c].x * l[c].x + x[c].y * l[c].y);
-            acc[0] += 0.5 * ek + D.energy_density(x, double(V), pp);
+            for (int c = 0; c < C; ++c) ek += x[c].x * l[c].x + x[c].y * l[c].y;
+            acc[0].add(T(0.5) * ek + D.energy_density(x, V, pp));
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                acc[1 + c] += double(cabs2(x[c]));
-                acc[1 + C + c] += double(x[c].x * o[c].x + x[c].y * o[c].y);
+                acc[1 + c].add(cabs2(x[c]));
+                acc[1 + C + c].add(x[c].x * o[c].x + x[c].y * o[c].y);
                 if (dst) dst[c * G + pt] = o[c];
             }
         } else {
@@ -338,16 +366,16 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
             hess_point<F, T2>(x, z, D, V, pp, l, o);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                T sh = T(a.sigslot >= 0 ? a.sigma * scal[a.sigslot] : a.sigma);
-                if (a.riem) sh -= T(scal[SBEC_S_ALPHA_G] + scal[SBEC_S_BETA_G] * double(F - c));
-                caxpy(o[c], sh, z[c]);
-                acc[c] += double(cabs2(x[c]));
-                acc[C + c] += double(x[c].x * o[c].x + x[c].y * o[c].y);
+                caxpy(o[c], shift[c], z[c]);
+                acc[c].add(cabs2(x[c]));
+                acc[C + c].add(x[c].x * o[c].x + x[c].y * o[c].y);
                 dst[c * G + pt] = o[c];
             }
         }
     }
-    block_reduce_store<NQ>(acc, a.partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[NQ];
+    acc_values(acc, v);
+    block_reduce_store<NQ>(v, a.partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -367,18 +395,18 @@ __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* 
     const long long foff = (long long)blockIdx.y * C * G;
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
-    double acc[2 * C];
-#pragma unroll
-    for (int q = 0; q < 2 * C; ++q) acc[q] = 0.0;
+    Acc<T> acc[2 * C];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const T2 u = U[c * G + p], w = Wv[c * G + p];
-            acc[c] += double(cabs2(u));
-            acc[C + c] += double(u.x * w.x + u.y * w.y);
+            acc[c].add(cabs2(u));
+            acc[C + c].add(u.x * w.x + u.y * w.y);
         }
     }
-    block_reduce_store<2 * C>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[2 * C];
+    acc_values(acc, v);
+    block_reduce_store<2 * C>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // out_l = W_l - (alpha + beta l) U_l with (alpha, beta) = scal[ia], scal[ib]; partial |out|^2
@@ -397,18 +425,20 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
     T coef[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) coef[c] = T(scal[ia] + scal[ib] * double(F - c));
-    double acc[1] = {0.0};
+    Acc<T> acc[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const T2 u = U[c * G + p];
             T2 w = Wv[c * G + p];
             caxpy(w, -coef[c], u);
-            acc[0] += double(cabs2(w));
+            acc[0].add(cabs2(w));
             if (O) O[c * G + p] = w;
         }
     }
-    block_reduce_store<1>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[1];
+    acc_values(acc, v);
+    block_reduce_store<1>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // w = U + t Xi into out; partials m_l = |w_l|^2
@@ -423,20 +453,20 @@ __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* X
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
     T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
-    double acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    Acc<T> acc[C];
     const T tt = T(t);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             T2 w = U[c * G + p];
             caxpy(w, tt, Xi[c * G + p]);
-            acc[c] += double(cabs2(w));
+            acc[c].add(cabs2(w));
             O[c * G + p] = w;
         }
     }
-    block_reduce_store<C>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[C];
+    acc_values(acc, v);
+    block_reduce_store<C>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // out_l *= scal[S_SIG + l]
@@ -702,7 +732,7 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
     if (L.ib >= 0) cb *= scal[L.ib];
     const bool upd = (L.guard < 0) || (scal[L.guard] != 0.0);
     const T a = T(ca), b = T(cb);
-    double acc[2] = {0.0, 0.0};
+    Acc<T> acc[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         T v;
         if (upd) {
@@ -712,10 +742,14 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
         } else {
             v = O[i];
         }
-        if (D1) acc[0] += double(v) * (self1 ? double(v) : double(D1[i]));
-        if (D2) acc[1] += double(v) * (self2 ? double(v) : double(D2[i]));
+        if (D1) acc[0].add(v * (self1 ? v : D1[i]));
+        if (D2) acc[1].add(v * (self2 ? v : D2[i]));
     }
-    if (partials) block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    if (partials) {
+        double r[2];
+        acc_values(acc, r);
+        block_reduce_store<2>(r, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    }
 }
 
 // partials q0 = <A, B>, q1 = <C, D> (C null: skip)
@@ -728,12 +762,14 @@ __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, co
     const T* __restrict__ B = reinterpret_cast<const T*>(Bp) + off;
     const T* __restrict__ Cv = Cp ? reinterpret_cast<const T*>(Cp) + off : nullptr;
     const T* __restrict__ D = Dp ? reinterpret_cast<const T*>(Dp) + off : nullptr;
-    double acc[2] = {0.0, 0.0};
+    Acc<T> acc[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        acc[0] += double(A[i]) * double(B[i]);
-        if (Cv) acc[1] += double(Cv[i]) * double(D[i]);
+        acc[0].add(A[i] * B[i]);
+        if (Cv) acc[1].add(Cv[i] * D[i]);
     }
-    block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[2];
+    acc_values(acc, v);
+    block_reduce_store<2>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // partials q0 = <u - up, g - gp>, q1 = |g - gp|^2 (the BB quantities s^T v, v^T v)
@@ -746,14 +782,16 @@ __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp,
     const T* __restrict__ UP = reinterpret_cast<const T*>(UPp) + off;
     const T* __restrict__ G = reinterpret_cast<const T*>(Gp) + off;
     const T* __restrict__ GP = reinterpret_cast<const T*>(GPp) + off;
-    double acc[2] = {0.0, 0.0};
+    Acc<T> acc[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const double sv = double(U[i]) - double(UP[i]);
-        const double vv = double(G[i]) - double(GP[i]);
-        acc[0] += sv * vv;
-        acc[1] += vv * vv;
+        const T sv = U[i] - UP[i];
+        const T vv = G[i] - GP[i];
+        acc[0].add(sv * vv);
+        acc[1].add(vv * vv);
     }
-    block_reduce_store<2>(acc, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v[2];
+    acc_values(acc, v);
+    block_reduce_store<2>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2), per instance
@@ -1034,7 +1072,7 @@ template <typename T>
 static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void* out, double* part) {
     SArgs a;
     a.in = in; a.out = out; a.tw = g.tw[axis];
-    for (int i = 0; i < 3; ++i) a.lam2[i] = g.lam2[i];
+    for (int i = 0; i < 3; ++i) { a.lam2[i] = g.lam2[i]; a.k2t[i] = g.k2s[i]; }
     a.G = g.G; a.axis = axis; a.logn = g.logn[axis]; a.W = c.W;
     a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
     a.ntx = g.n[0] / c.W;
@@ -1051,7 +1089,7 @@ template <typename T>
 static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, double* part) {
     XArgs a;
     a.in = in; a.out = out; a.X = nullptr; a.Zd = nullptr; a.V = g.V; a.tw = g.tw[0];
-    a.lam2x = g.lam2[0]; a.G = g.G; a.logn = g.logn[0]; a.rpb = c.rpb; a.invG = g.invG;
+    a.lam2x = g.lam2[0]; a.k2x = g.k2s[0]; a.G = g.G; a.logn = g.logn[0]; a.rpb = c.rpb; a.invG = g.invG;
     a.sigma = 0.0; a.scal = nullptr; a.riem = 0; a.sigslot = -1;
     a.partials = part; a.nblk = c.nblk;
     a.pp = point_params(g);
