@@ -221,6 +221,148 @@ __device__ __forceinline__ void fft_pencils(T2* buf, int logn, int P, int ps, in
 }
 
 // ---------------------------------------------------------------------------
+// Register DFTs of length L = 1, 2, 4, 8, 16 (natural order in and out,
+// unnormalised; INV: the conjugate transform), built from 4-point butterflies.
+// W16[e] = exp(-2 pi i e / 16) is exact to double rounding: cos and sin of
+// multiples of pi/8 are 1, sqrt(1/2), cos(pi/8) = sqrt(2 + sqrt 2)/2 and
+// sin(pi/8) = sqrt(2 - sqrt 2)/2.
+// ---------------------------------------------------------------------------
+constexpr double kC8 = 0.92387953251128675613;   // cos(pi/8)
+constexpr double kS8 = 0.38268343236508977173;   // sin(pi/8)
+constexpr double kR2 = 0.70710678118654752440;   // sqrt(1/2)
+
+// a * W16^E (forward) or a * conj(W16^E) (inverse)
+template <typename T2, bool INV, int E>
+__device__ __forceinline__ T2 mul_w16(T2 a) {
+    using T = decltype(T2::x);
+    constexpr int e = E & 15;
+    if constexpr (e == 0) {
+        return a;
+    } else if constexpr (e == 4) {
+        return INV ? mk<T2>(-a.y, a.x) : mk<T2>(a.y, -a.x);        // -i (forward)
+    } else if constexpr (e == 8) {
+        return mk<T2>(-a.x, -a.y);
+    } else if constexpr (e == 12) {
+        return INV ? mk<T2>(a.y, -a.x) : mk<T2>(-a.y, a.x);        // +i (forward)
+    } else {
+        constexpr double cs[16] = {1, kC8, kR2, kS8, 0, -kS8, -kR2, -kC8, -1, -kC8, -kR2, -kS8, 0, kS8, kR2, kC8};
+        constexpr double sn[16] = {0, kS8, kR2, kC8, 1, kC8, kR2, kS8, 0, -kS8, -kR2, -kC8, -1, -kC8, -kR2, -kS8};
+        const T c = T(cs[e]), sg = T(INV ? -sn[e] : sn[e]);
+        // (a.x + i a.y)(c - i sg)
+        return mk<T2>(a.x * c + a.y * sg, a.y * c - a.x * sg);
+    }
+}
+
+template <typename T2, bool INV>
+__device__ __forceinline__ void dft4(T2& a0, T2& a1, T2& a2, T2& a3) {
+    const T2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+    const T2 t3 = mul_w16<T2, INV, 4>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+template <typename T2, int L, bool INV> struct RegDft;
+template <typename T2, bool INV> struct RegDft<T2, 1, INV> {
+    __device__ static __forceinline__ void run(T2*) {}
+};
+template <typename T2, bool INV> struct RegDft<T2, 2, INV> {
+    __device__ static __forceinline__ void run(T2* v) {
+        const T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <typename T2, bool INV> struct RegDft<T2, 4, INV> {
+    __device__ static __forceinline__ void run(T2* v) { dft4<T2, INV>(v[0], v[1], v[2], v[3]); }
+};
+// 8 = 2 x 4: X[k] = E[k] + W8^k O[k], X[k + 4] = E[k] - W8^k O[k]
+template <typename T2, bool INV> struct RegDft<T2, 8, INV> {
+    __device__ static __forceinline__ void run(T2* v) {
+        T2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4<T2, INV>(e0, e1, e2, e3);
+        dft4<T2, INV>(o0, o1, o2, o3);
+        o1 = mul_w16<T2, INV, 2>(o1);
+        o2 = mul_w16<T2, INV, 4>(o2);
+        o3 = mul_w16<T2, INV, 6>(o3);
+        v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+        v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+        v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+        v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+    }
+};
+// 16 = 4 x 4: j = j1 + 4 j2, k = k2 + 4 k1; DFT4 over j2, times W16^{j1 k2},
+// DFT4 over j1
+template <typename T2, bool INV> struct RegDft<T2, 16, INV> {
+    __device__ static __forceinline__ void run(T2* v) {
+#pragma unroll
+        for (int j1 = 0; j1 < 4; ++j1) dft4<T2, INV>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12]);
+        // v[j1 + 4 k2] *= W16^{j1 k2}
+        v[5] = mul_w16<T2, INV, 1>(v[5]);
+        v[9] = mul_w16<T2, INV, 2>(v[9]);
+        v[13] = mul_w16<T2, INV, 3>(v[13]);
+        v[6] = mul_w16<T2, INV, 2>(v[6]);
+        v[10] = mul_w16<T2, INV, 4>(v[10]);
+        v[14] = mul_w16<T2, INV, 6>(v[14]);
+        v[7] = mul_w16<T2, INV, 3>(v[7]);
+        v[11] = mul_w16<T2, INV, 6>(v[11]);
+        v[15] = mul_w16<T2, INV, 9>(v[15]);
+        T2 r[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            T2 a0 = v[4 * k2], a1 = v[4 * k2 + 1], a2 = v[4 * k2 + 2], a3 = v[4 * k2 + 3];
+            dft4<T2, INV>(a0, a1, a2, a3);
+            r[k2] = a0; r[k2 + 4] = a1; r[k2 + 8] = a2; r[k2 + 12] = a3;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = r[i];
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Two-level FFT of length N = N1 N2 (N <= 256): with j = j1 + N1 j2 and
+// k = k2 + N2 k1,
+//   X[k2 + N2 k1] = sum_j1 W_N1^{j1 k1} W_N^{j1 k2} sum_j2 W_N2^{j2 k2} x[j1 + N1 j2].
+// Level A: one thread per j1 holds x[j1 + N1 j2] (j2 < N2) in registers, applies
+// DFT_N2 and the twiddles W_N^{j1 k2}; one exchange through shared memory; level
+// B: one thread per k2 holds the N1 values of its k2 and applies DFT_N1.  The
+// inverse runs the levels backwards with conjugate twiddles.  Each level is a
+// register computation; the only shared-memory traffic is the exchange.
+// ---------------------------------------------------------------------------
+template <int LOGN> struct Split2 {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int N1 = 1 << ((LOGN + 1) / 2);   // level-B length (>= N2)
+    static constexpr int N2 = N / N1;                   // level-A length
+};
+
+// level A forward: v[0..N2) = x[j1 + N1 j2] -> v[k2] = W_N^{j1 k2} DFT_N2(x)[k2]
+template <typename T2, int LOGN, bool INV>
+__device__ __forceinline__ void level_a_fwd(T2* v, int j1, const T2* __restrict__ tw) {
+    constexpr int N2 = Split2<LOGN>::N2;
+    RegDft<T2, N2, INV>::run(v);
+    if (j1 != 0) {
+#pragma unroll
+        for (int k2 = 1; k2 < N2; ++k2) {
+            T2 w = tw[j1 * k2];
+            if (INV) w = cconj(w);
+            v[k2] = cmul(v[k2], w);
+        }
+    }
+}
+
+// level B' (inverse start): v[0..N1) = X[k2 + N2 k1] -> v[j1] = W_N^{-j1 k2} IDFT_N1(X)[j1]
+template <typename T2, int LOGN>
+__device__ __forceinline__ void level_b_inv(T2* v, int k2, const T2* __restrict__ tw) {
+    constexpr int N1 = Split2<LOGN>::N1;
+    RegDft<T2, N1, true>::run(v);
+    if (k2 != 0) {
+#pragma unroll
+        for (int j1 = 1; j1 < N1; ++j1) v[j1] = cmul(v[j1], cconj(tw[j1 * k2]));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Spin-F constants in ladder / pair form (an independent restatement of the
 // Sec. 2 matrices).  Component index i = 0..2F holds l = F - i.
 //   LAD[i]  = sqrt(F(F+1) - (l-1) l) couples i and i+1:  F_+ = sum_i LAD[i] conj(x_i) x_{i+1}

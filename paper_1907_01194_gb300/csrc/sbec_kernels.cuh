@@ -317,6 +317,198 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Passes with the two-level FFT (lengths n = 2^LOGN <= 256).  Level A reads its
+// values straight from global memory and level A' writes them straight back;
+// the level-B values of one k2 stay in registers, so the k-space scaling of
+// S_K2 and the Parseval sum touch no shared memory.  The one exchange per
+// transform goes through the block's shared-memory tile.
+// ---------------------------------------------------------------------------
+
+// Strided pass: W pencils (consecutive x) of one component along the pass axis;
+// thread (w, q), w = tid mod W, blockDim.x = W N1 <= 256.  Exchange slot of element
+// (e1, e2) of pencil w: sm[e2 * rs + e1 * W + w], rs = N1 W + pad; pad = W for
+// W < 16 puts the level-B reads of a half-warp on distinct banks.
+template <typename T, int MODE, int LOGN>
+__global__ void __launch_bounds__(256, 2) k_spass2(const SArgs a) {
+    using T2 = typename C2<T>::t;
+    constexpr int N1 = Split2<LOGN>::N1, N2 = Split2<LOGN>::N2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* sm = reinterpret_cast<T2*>(smem_raw);
+    const int W = a.W;
+    const int w = threadIdx.x & (W - 1), q = threadIdx.x / W;
+    long long b = blockIdx.x;
+    const int xt = (int)(b % a.ntx); b /= a.ntx;
+    const int o = (int)(b % a.nouter);
+    const int c = (int)(b / a.nouter);
+    if (skipped(a.skip, c / a.C)) return;
+    const long long obase = (a.axis == 1) ? (long long)o * a.ny * a.nx : (long long)o * a.nx;
+    const long long base = (long long)c * a.G + obase + (long long)xt * W + w;
+    const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + base;
+    const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
+    const long long es = a.estride;
+    const int rs = N1 * W + (W < 16 ? W : 0);
+    T2 v[N1];
+    if (MODE != S_INV) {
+#pragma unroll
+        for (int j2 = 0; j2 < N2; ++j2) v[j2] = src[(long long)(q + N1 * j2) * es];
+        level_a_fwd<T2, LOGN, false>(v, q, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) sm[k2 * rs + q * W + w] = v[k2];
+        __syncthreads();
+        if (q < N2) {
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = sm[q * rs + j1 * W + w];
+            RegDft<T2, N1, false>::run(v);            // v[k1] = X[q + N2 k1]
+        }
+    }
+    if (MODE == S_FWD) {
+        T2* __restrict__ dst = reinterpret_cast<T2*>(a.out) + base;
+        if (q < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) dst[(long long)(q + N2 * k1) * es] = v[k1];
+        }
+        return;
+    }
+    if (MODE == S_K2 || MODE == S_PARSEVAL) {
+        Acc<T> acc[1];
+        if (q < N2) {
+            const int ix = xt * W + w;
+            const bool ya = (a.axis == 1);
+            if constexpr (sizeof(T) == 8) {
+                // |k|^2 = (lam_x + lam_y) + lam_z, the pass axis' term from the table
+                const double lx = a.lam2[0][ix], lo = a.lam2[ya ? 2 : 1][o];
+                const double* __restrict__ le = a.lam2[a.axis];
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    const double l = le[q + N2 * k1];
+                    const double k2 = ya ? (lx + l) + lo : (lx + lo) + l;
+                    if (MODE == S_K2) v[k1] = cscale(v[k1], T(k2 * a.invG));
+                    else acc[0].add(0.5 * a.invG * k2 * cabs2(v[k1]));
+                }
+            } else {
+                const T f0 = reinterpret_cast<const T*>(a.k2t[0])[ix] +
+                             reinterpret_cast<const T*>(a.k2t[ya ? 2 : 1])[o];
+                const T* __restrict__ fe = reinterpret_cast<const T*>(a.k2t[a.axis]);
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) {
+                    const T f = f0 + fe[q + N2 * k1];
+                    if (MODE == S_K2) v[k1] = cscale(v[k1], f);
+                    else acc[0].add(T(0.5) * f * cabs2(v[k1]));
+                }
+            }
+        }
+        if (MODE == S_PARSEVAL) {
+            double r[1];
+            acc_values(acc, r);
+            block_reduce_store<1>(r, a.partials, a.nblk, blockIdx.x);
+            return;
+        }
+    }
+    if (MODE == S_INV && q < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = src[(long long)(q + N2 * k1) * es];
+    }
+    // inverse: level B' (k2 = q; its slots are this thread's own), exchange, level A'
+    if (q < N2) {
+        level_b_inv<T2, LOGN>(v, q, tw);
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) sm[q * rs + j1 * W + w] = v[j1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) v[k2] = sm[k2 * rs + q * W + w];
+    RegDft<T2, N2, true>::run(v);                     // v[j2] = x[q + N1 j2]
+    T2* __restrict__ dst = reinterpret_cast<T2*>(a.out) + base;
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) dst[(long long)(q + N1 * j2) * es] = v[j2];
+}
+
+// x pass of 2D / 3D problems (X_FWD, X_FWD_EPW, X_INV): rpb grid rows of all C
+// components; pencil p = row group * C + component, thread (p, q) with
+// q = tid mod N1 (threads with p >= P only join the barriers and sums).
+// Exchange slot of element (e1, e2) of pencil p: sm[p * S + e2 (N1 + 1) + e1],
+// S = N2 (N1 + 1); the +1 spreads the level-B reads over the banks.
+template <typename T, int F, int MODE, int LOGN>
+__global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    constexpr int N = 1 << LOGN, N1 = Split2<LOGN>::N1, N2 = Split2<LOGN>::N2;
+    constexpr int S = N2 * (N1 + 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* sm = reinterpret_cast<T2*>(smem_raw);
+    const int RPB = a.rpb, P = RPB * C;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int p = tid / N1, q = tid & (N1 - 1);
+    const bool on = p < P;
+    const long long growrow = (long long)blockIdx.x * RPB;
+    const long long inst = growrow / a.rpi;
+    const long long row0 = growrow - inst * a.rpi;
+    const long long foff = inst * (long long)C * a.G;
+    if (skipped(a.skip, inst)) return;
+    const int rg = p / C, cc = p - rg * C;
+    const long long roff = foff + (long long)cc * a.G + (row0 + rg) * N;
+    const T2* __restrict__ row = reinterpret_cast<const T2*>(a.in) + (on ? roff : 0);
+    T2* __restrict__ orow = reinterpret_cast<T2*>(a.out) + (on ? roff : 0);
+    const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
+    T2* my = sm + p * S;
+    Acc<T> acc[1];
+    if (MODE == X_FWD_EPW) {
+        // pointwise energy density of the block's input points (Eq. 3.7 without the kinetic term)
+        const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + foff;
+        const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * a.G;
+        const PPT<T> pp(a.ppb ? a.ppb[inst] : a.pp);
+        for (int idx = tid; idx < RPB * N; idx += nth) {
+            const long long pt = (row0 + (idx >> LOGN)) * N + (idx & (N - 1));
+            T2 x[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) x[c] = src[(long long)c * a.G + pt];
+            Dens<F, T2> D;
+            D.compute(x);
+            acc[0].add(D.energy_density(x, Vp[pt], pp));
+        }
+    }
+    T2 v[N1];
+    if (MODE != X_INV) {
+        if (on) {
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) v[j2] = row[q + N1 * j2];
+            level_a_fwd<T2, LOGN, false>(v, q, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) my[k2 * (N1 + 1) + q] = v[k2];
+        }
+        __syncthreads();
+        if (on && q < N2) {
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = my[q * (N1 + 1) + j1];
+            RegDft<T2, N1, false>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) orow[q + N2 * k1] = v[k1];
+        }
+    } else {
+        if (on && q < N2) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) v[k1] = row[q + N2 * k1];
+            level_b_inv<T2, LOGN>(v, q, tw);
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) my[q * (N1 + 1) + j1] = v[j1];
+        }
+        __syncthreads();
+        if (on) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) v[k2] = my[k2 * (N1 + 1) + q];
+            RegDft<T2, N2, true>::run(v);
+#pragma unroll
+            for (int j2 = 0; j2 < N2; ++j2) orow[q + N1 * j2] = v[j2];
+        }
+    }
+    if (MODE == X_FWD_EPW) {
+        double r[1];
+        acc_values(acc, r);
+        block_reduce_store<1>(r, a.partials, a.nblk, blockIdx.x);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stand-alone epilogues (used when the inverse x pass only transforms): the
 // gradient (Eq. 3.12) or Hessian-vector product (Eq. 3.13) of every grid point
 // from L X (or L Z) in `lx`, with the same partial sums as the fused x pass.
@@ -896,8 +1088,10 @@ __global__ void k_convert(void* Vp, const double* Vd, long long G) {
 // ---------------------------------------------------------------------------
 // Launch configuration
 // ---------------------------------------------------------------------------
-struct XCfg { int rpb, nth, items, nblk, nblk_inst; size_t smem; };
-struct SCfg { int W, nth, items, nblk, nblk_inst; size_t smem; };
+// two: the pass runs the two-level FFT kernel (k_xpass2 / k_spass2) of length 2^logn
+struct XCfg { int rpb, nth, items, nblk, nblk_inst, two, logn; size_t smem; };
+struct SCfg { int W, nth, items, nblk, nblk_inst, two, logn; size_t smem; };
+constexpr int kMaxLogn2 = 8;   // longest two-level FFT: 256 points
 
 // Limits of the launch shapes: at most 4096 butterflies per block (512 threads x 8
 // items) and the opt-in dynamic shared memory of one block.
@@ -915,6 +1109,24 @@ template <typename T>
 static XCfg xcfg(const Geom& g) {
     const int n = g.n[0];
     const long long rows_inst = g.G / n;
+    if (g.dim > 1 && g.logn[0] >= 1 && g.logn[0] <= kMaxLogn2) {
+        // two-level FFT: N1 threads per row, all C components of rpb rows per block
+        const int lg = g.logn[0];
+        const int N1 = 1 << ((lg + 1) / 2), N2 = n / N1;
+        int rpb = 1;
+        if (g.tune.x_rows > 0) {
+            rpb = g.tune.x_rows;
+        } else {
+            while ((long long)rpb * 2 * g.C * N1 <= 256 && rows_inst % (rpb * 2) == 0) rpb *= 2;
+        }
+        XCfg c;
+        c.two = 1; c.logn = lg; c.rpb = rpb; c.items = 0;
+        c.nth = ((rpb * g.C * N1 + 31) / 32) * 32;
+        c.nblk_inst = (int)(rows_inst / rpb);
+        c.nblk = c.nblk_inst * g.B;
+        c.smem = (size_t)rpb * g.C * N2 * (N1 + 1) * sizeof(typename C2<T>::t);
+        return c;
+    }
     int rpb = 1;
     if (g.tune.x_rows > 0) {
         rpb = g.tune.x_rows;
@@ -930,6 +1142,7 @@ static XCfg xcfg(const Geom& g) {
     int it2 = 1;
     while (it2 < items) it2 *= 2;
     XCfg c;
+    c.two = 0; c.logn = g.logn[0];
     c.rpb = rpb; c.nth = nth; c.items = it2;
     c.nblk_inst = (int)(rows_inst / rpb);
     c.nblk = c.nblk_inst * g.B;
@@ -952,6 +1165,20 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
         // prefer at least 4 blocks per SM when the grid is small
         while (W > 2 && (long long)g.B * g.C * outer * (nx / W) < 4LL * num_sms) W >>= 1;
     }
+    const int lg = g.logn[axis];
+    if (lg >= 1 && lg <= kMaxLogn2) {
+        // two-level FFT: N1 threads per pencil, whole warps, at most 256 threads
+        // (k_spass2's launch bound: two such blocks per SM)
+        const int N1 = 1 << ((lg + 1) / 2), N2 = n / N1;
+        if ((W * N1) % 32 == 0 && W * N1 <= 256) {
+            SCfg c;
+            c.two = 1; c.logn = lg; c.W = W; c.nth = W * N1; c.items = 0;
+            c.nblk_inst = (int)((long long)g.C * outer * (nx / W));
+            c.nblk = c.nblk_inst * g.B;
+            c.smem = (size_t)N2 * (N1 * W + (W < 16 ? W : 0)) * sizeof(T2);
+            return c;
+        }
+    }
     const int bfly = (n >= 4) ? W * n / 4 : W;
     const int split = g.tune.s_split[axis] > 0 ? g.tune.s_split[axis] : 1;
     int nth = ((bfly / split + 31) / 32) * 32;
@@ -961,6 +1188,7 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
     int it2 = 1;
     while (it2 < items) it2 *= 2;
     SCfg c;
+    c.two = 0; c.logn = lg;
     c.W = W; c.nth = nth; c.items = it2;
     c.nblk_inst = (int)((long long)g.C * outer * (nx / W));
     c.nblk = c.nblk_inst * g.B;
@@ -1027,8 +1255,36 @@ static int launch_x_items(const XCfg& c, const XArgs& a, const Work& w, cudaStre
     return SBEC_OK;
 }
 
+template <typename T, int F, int MODE, int LOGN>
+static int launch_x2(const XCfg& c, const XArgs& a, const Work& w, cudaStream_t s) {
+    auto kern = k_xpass2<T, F, MODE, LOGN>;
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, c.smem, granted)) return st;
+    ProfScope ps(w.prof, XKid<MODE>::v, s);
+    kern<<<c.nblk, c.nth, c.smem, s>>>(a);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
 template <typename T, int F, int MODE>
 static int launch_x(const XCfg& c, const XArgs& a, const Work& w, cudaStream_t s) {
+    if constexpr (MODE == X_FWD || MODE == X_FWD_EPW || MODE == X_INV) {
+        if (c.two) {
+            switch (c.logn) {
+                case 1: return launch_x2<T, F, MODE, 1>(c, a, w, s);
+                case 2: return launch_x2<T, F, MODE, 2>(c, a, w, s);
+                case 3: return launch_x2<T, F, MODE, 3>(c, a, w, s);
+                case 4: return launch_x2<T, F, MODE, 4>(c, a, w, s);
+                case 5: return launch_x2<T, F, MODE, 5>(c, a, w, s);
+                case 6: return launch_x2<T, F, MODE, 6>(c, a, w, s);
+                case 7: return launch_x2<T, F, MODE, 7>(c, a, w, s);
+                case 8: return launch_x2<T, F, MODE, 8>(c, a, w, s);
+                default: return SBEC_ERR_ARG;
+            }
+        }
+    } else {
+        if (c.two) return SBEC_ERR_ARG;
+    }
     switch (c.items) {
         case 1: return launch_x_items<T, F, MODE, 1>(c, a, w, s);
         case 2: return launch_x_items<T, F, MODE, 2>(c, a, w, s);
@@ -1049,8 +1305,32 @@ static int launch_s_items(const SCfg& c, const SArgs& a, const Work& w, cudaStre
     return SBEC_OK;
 }
 
+template <typename T, int MODE, int LOGN>
+static int launch_s2(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
+    auto kern = k_spass2<T, MODE, LOGN>;
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, c.smem, granted)) return st;
+    ProfScope ps(w.prof, SKid<MODE>::v, s);
+    kern<<<c.nblk, c.nth, c.smem, s>>>(a);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
 template <typename T, int MODE>
 static int launch_s(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
+    if (c.two) {
+        switch (c.logn) {
+            case 1: return launch_s2<T, MODE, 1>(c, a, w, s);
+            case 2: return launch_s2<T, MODE, 2>(c, a, w, s);
+            case 3: return launch_s2<T, MODE, 3>(c, a, w, s);
+            case 4: return launch_s2<T, MODE, 4>(c, a, w, s);
+            case 5: return launch_s2<T, MODE, 5>(c, a, w, s);
+            case 6: return launch_s2<T, MODE, 6>(c, a, w, s);
+            case 7: return launch_s2<T, MODE, 7>(c, a, w, s);
+            case 8: return launch_s2<T, MODE, 8>(c, a, w, s);
+            default: return SBEC_ERR_ARG;
+        }
+    }
     switch (c.items) {
         case 1: return launch_s_items<T, MODE, 1>(c, a, w, s);
         case 2: return launch_s_items<T, MODE, 2>(c, a, w, s);
@@ -1436,8 +1716,15 @@ bool Ops<T>::tune_ok(const Geom& g, const Tune& t) {
     if (t.x_rows != 0) {
         const long long rows_inst = g.G / g.n[0];
         if (!pow2(t.x_rows) || rows_inst % t.x_rows != 0) return false;
-        const long long pts = (long long)t.x_rows * g.C * g.n[0];
-        if (pts > kMaxPointsPerBlock || xsmem<T>(t.x_rows * g.C, g.n[0]) > kMaxSmem) return false;
+        Geom h = g;
+        h.tune = t;
+        const XCfg c = xcfg<T>(h);
+        if (c.two) {
+            if (c.nth > 512 || c.smem > kMaxSmem) return false;
+        } else {
+            const long long pts = (long long)t.x_rows * g.C * g.n[0];
+            if (pts > kMaxPointsPerBlock || xsmem<T>(t.x_rows * g.C, g.n[0]) > kMaxSmem) return false;
+        }
     }
     if (t.s_pencils[0] != 0 || t.s_split[0] != 0) return false;
     for (int ax = 1; ax < 3; ++ax) {
@@ -1446,6 +1733,13 @@ bool Ops<T>::tune_ok(const Geom& g, const Tune& t) {
         if (sp != 0 && sp != 1 && sp != 2 && sp != 4 && sp != 8) return false;
         if (W == 0) continue;
         if (!pow2(W) || W > g.n[0]) return false;
+        Geom h = g;
+        h.tune = t;
+        const SCfg c = scfg<T>(h, ax, 1);
+        if (c.two) {
+            if (c.nth > 512 || c.smem > kMaxSmem) return false;
+            continue;
+        }
         const long long pts = (long long)W * g.n[ax];
         if (pts > kMaxPointsPerBlock || (size_t)pts * sizeof(typename C2<T>::t) > kMaxSmem) return false;
     }

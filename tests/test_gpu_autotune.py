@@ -34,14 +34,15 @@ W2 = _wl(2, (64, 32), 8.0, 0.3, (200.0, 10.0, -5.0, 0), lattice=20.0)
 W3 = _wl(3, (16, 8, 32), 6.0, 0.2, (500.0, -2.0, 5.0, -1.0))
 
 # explicit shapes spanning the accepted range (small and large tiles, split
-# butterflies, few and many elementwise blocks)
+# butterflies, few and many elementwise blocks); tiles of more than 256 threads
+# run the shared-memory Stockham kernels, smaller ones the two-level kernels
 SHAPES = {
     W1.name: [dict(x_rows=1, elem_per_sm=1), dict(x_rows=1, elem_per_sm=32)],
     W2.name: [dict(x_rows=1, s_pencils=[0, 1, 0], s_split=[0, 4, 0], elem_per_sm=2),
-              dict(x_rows=32, s_pencils=[0, 64, 0], s_split=[0, 1, 0], elem_per_sm=32),
+              dict(x_rows=8, s_pencils=[0, 64, 0], s_split=[0, 1, 0], elem_per_sm=32),
               dict(x_rows=4, s_pencils=[0, 8, 0], s_split=[0, 8, 0])],
     W3.name: [dict(x_rows=1, s_pencils=[0, 1, 1], s_split=[0, 2, 4], elem_per_sm=3),
-              dict(x_rows=64, s_pencils=[0, 16, 16], s_split=[0, 1, 8], elem_per_sm=32)],
+              dict(x_rows=16, s_pencils=[0, 16, 16], s_split=[0, 1, 8], elem_per_sm=32)],
 }
 
 
@@ -95,7 +96,7 @@ def test_invalid_shapes_are_rejected(dev):
     from paper_1907_01194_gb300 import sbec
     with sbec.Handle.from_workload(W2) as h:
         before = h.get_tune()
-        for bad in (dict(x_rows=3), dict(x_rows=128), dict(s_pencils=[0, 128, 0]), dict(s_pencils=[0, 3, 0]),
+        for bad in (dict(x_rows=3), dict(x_rows=16), dict(s_pencils=[0, 128, 0]), dict(s_pencils=[0, 3, 0]),
                     dict(s_split=[0, 3, 0]), dict(s_pencils=[0, 0, 4]), dict(s_pencils=[2, 0, 0]),
                     dict(elem_per_sm=33), dict(elem_per_sm=-1)):
             with pytest.raises(sbec.SbecError):

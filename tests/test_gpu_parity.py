@@ -40,6 +40,8 @@ CASES = [
     _wl(3, (16, 8, 32), 6.0, 0.2, (500.0, -2.0, 5.0, -1.0)),              # 3D non-cubic
     _wl(2, (32, 32, 32), 8.0, 0.0, (100.0, 3.0, 4.0, 0), lattice=10.0),   # 3D, M = 0
     _wl(1, (1024,), 20.0, 0.4, (300.0, 2.0, 0, 0)),                       # longest axis
+    _wl(2, (512, 4), 12.0, 0.3, (80.0, 2.0, -1.0, 0)),                     # long x rows in 2D
+    _wl(1, (4, 8, 512), 6.0, 0.1, (40.0, 1.0, 0, 0)),                      # long strided axis
 ]
 
 
