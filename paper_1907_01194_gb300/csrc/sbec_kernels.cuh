@@ -513,12 +513,40 @@ __global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
 // gradient (Eq. 3.12) or Hessian-vector product (Eq. 3.13) of every grid point
 // from L X (or L Z) in `lx`, with the same partial sums as the fused x pass.
 // blockIdx.y is the instance; partials of instance b are blocks b*gridDim.x ...
+//
+// The inputs of a point (X, L X, Z: C values each, and V) reach shared memory by
+// per-thread asynchronous copies (cp.async) one grid-stride step ahead: while a
+// thread computes point k, the copies of point k + 1 are in flight, so the
+// register-heavy pointwise algebra (one or two blocks per SM) overlaps the HBM
+// traffic.  Each thread reads back only the slots it copied itself.
 // ---------------------------------------------------------------------------
+constexpr int kEpiThreads = 256;
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename T, int F, bool HESS>
-__global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp, long long G) {
+constexpr size_t epi_smem() {
+    return 2 * ((size_t)(HESS ? 3 : 2) * (2 * F + 1) * kEpiThreads * sizeof(typename C2<T>::t) +
+                (size_t)kEpiThreads * sizeof(T));
+}
+
+template <typename T, int F, bool HESS>
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const void* lxp, long long G) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
+    constexpr int NA = HESS ? 3 : 2;                  // staged arrays X, L X (, Z)
+    constexpr int P = kEpiThreads;
     const long long inst = blockIdx.y;
     const long long foff = inst * (long long)C * G;
     const T2* __restrict__ LX = reinterpret_cast<const T2*>(lxp) + foff;
@@ -529,14 +557,38 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
     const PPT<T> pp(a.ppb ? a.ppb[inst] : a.pp);
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
     if (skipped(a.skip, inst)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* stg = reinterpret_cast<T2*>(smem_raw);                       // [2][NA C][P]
+    T* vst = reinterpret_cast<T*>(stg + 2 * NA * C * P);             // [2][P]
+    const int tid = threadIdx.x;
     T shift[C];
     if (HESS) hess_shift<F, T>(a, scal, shift);
     Acc<T> acc[NQ];
-    for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < G; pt += (long long)gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * P;
+    // copies of point p into stage st (none past the end; the group is committed anyway)
+    auto issue = [&](long long p, int st) {
+        if (p < G) {
+            T2* d = stg + (size_t)st * NA * C * P + tid;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                cp_async<sizeof(T2)>(d + c * P, Xp + c * G + p);
+                cp_async<sizeof(T2)>(d + (C + c) * P, LX + c * G + p);
+                if (HESS) cp_async<sizeof(T2)>(d + (2 * C + c) * P, Zp + c * G + p);
+            }
+            cp_async<sizeof(T)>(vst + st * P + tid, Vp + p);
+        }
+        cp_async_commit();
+    };
+    long long pt = (long long)blockIdx.x * P + tid;
+    issue(pt, 0);
+    for (int k = 0; pt < G; ++k, pt += stride) {
+        issue(pt + stride, (k + 1) & 1);
+        cp_async_wait<1>();                          // this thread's copies of point pt are in
+        const T2* sx = stg + (size_t)(k & 1) * NA * C * P + tid;
         T2 x[C], l[C], o[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) { x[c] = Xp[c * G + pt]; l[c] = LX[c * G + pt]; }
-        const T V = Vp[pt];
+        for (int c = 0; c < C; ++c) { x[c] = sx[c * P]; l[c] = sx[(C + c) * P]; }
+        const T V = vst[(k & 1) * P + tid];
         Dens<F, T2> D;
         D.compute(x);
         if (!HESS) {
@@ -554,7 +606,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
         } else {
             T2 z[C];
 #pragma unroll
-            for (int c = 0; c < C; ++c) z[c] = Zp[c * G + pt];
+            for (int c = 0; c < C; ++c) z[c] = sx[(2 * C + c) * P];
             hess_point<F, T2>(x, z, D, V, pp, l, o);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -565,6 +617,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const XArgs a, const void* lxp
             }
         }
     }
+    cp_async_wait<0>();                              // no copy outlives the block
     double v[NQ];
     acc_values(acc, v);
     block_reduce_store<NQ>(v, a.partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
@@ -1348,6 +1401,18 @@ static int launch_s(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s
         SBEC_LAUNCH_CHECK();                                \
     } while (0)
 
+template <typename T, int F, bool HESS>
+static int launch_epi(const Geom& g, const Work& w, const XArgs& a, int ne, cudaStream_t s) {
+    auto kern = k_epilogue<T, F, HESS>;
+    constexpr size_t smem = epi_smem<T, F, HESS>();
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, smem, granted)) return st;
+    ProfScope ps(w.prof, HESS ? K_X_INV_HESS : K_X_INV_GRAD, s);
+    kern<<<dim3(ne, g.B), kEpiThreads, smem, s>>>(a, w.work, g.G);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
 template <typename T>
 static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void* out, double* part) {
     SArgs a;
@@ -1423,7 +1488,8 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
             const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
             XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
             a.X = X;
-            SBEC_LAUNCH(K_X_INV_GRAD, (k_epilogue<T, F, false>), dim3(ne, g.B), 256, a, w.work, g.G);
+            st = launch_epi<T, F, false>(g, w, a, ne, s);
+            if (st) return st;
             SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
                         SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
             goto rgrad;
@@ -1509,7 +1575,8 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
             st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
             if (st) return st;
             const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-            SBEC_LAUNCH(K_X_INV_HESS, (k_epilogue<T, F, true>), dim3(ne, g.B), 256, a, w.work, g.G);
+            st = launch_epi<T, F, true>(g, w, a, ne, s);
+            if (st) return st;
             if (riem) {
                 SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
                             S_PA, S_PB, 0);
