@@ -254,8 +254,12 @@ def bytes_model(w, kname, elem, B=1):
 
 
 def roofline_of(prof, w, precision, B, wname):
+    # the dominant kernel among those with an algorithmic model (the scalar finalize and
+    # retraction-solve kernels have none: they are launch-latency work)
     total = sum(v[0] for v in prof.values())
-    kname, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    modelled = {k: v for k, v in prof.items()
+                if (flops_model(w, k, B) if precision == "fp64" else bytes_model(w, k, 8, B))}
+    kname, (kms, kcnt) = max((modelled or prof).items(), key=lambda kv: kv[1][0])
     per_launch_s = kms / kcnt * 1e-3
     if precision == "fp64":
         fl = flops_model(w, kname, B)

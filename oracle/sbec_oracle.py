@@ -633,7 +633,9 @@ def rgbb(P: Problem, u, opts: SolveOptions, tol, maxit, stats: SolveStats):
     Readings: gamma_0 = opts.rgbb_gamma0 on the first step; the BB step is
     clamped to [1e-10, 1e10]; s and v are plain differences (no transport); at
     most opts.rgbb_max_backtracks reductions, after which the last trial is
-    taken.
+    taken; a trial whose energy differs from the current one by no more than
+    the rounding floor noise_factor * eps * max(1, |E|) passes the test (the
+    floor the ARNT search uses).
     """
     kind = opts.retraction
     E = E_u(P, u)
@@ -659,11 +661,12 @@ def rgbb(P: Problem, u, opts: SolveOptions, tol, maxit, stats: SolveStats):
             gam = min(max(gam, 1e-10), 1e10)
         slope = rg @ eta                                   # <grad, eta> = -||grad||^2
         t = gam
+        noise = opts.noise_factor * np.finfo(float).eps * max(1.0, abs(E))
         for _ in range(opts.rgbb_max_backtracks + 1):
             z = retract(P, u, t * eta, kind)
             Ez = E_u(P, z)
             stats.n_energy += 1
-            if Ez <= C + opts.rgbb_rho * t * slope:
+            if Ez <= C + opts.rgbb_rho * t * slope or abs(Ez - E) <= noise:
                 break
             t *= opts.rgbb_delta
         u_prev, rg_prev = u, rg

@@ -374,6 +374,14 @@ __device__ __forceinline__ void level_b_inv(T2* v, int k2, const T2* __restrict_
 // ---------------------------------------------------------------------------
 template <int F> struct Spin;
 
+// 1 / sqrt(2F + 1), the singlet normalisation (a literal: a device sqrt of a
+// constant is not folded at compile time and would cost an FP64 square root and
+// division per grid point)
+template <int C> struct InvSqrtC;
+template <> struct InvSqrtC<3> { static constexpr double v = 0.57735026918962576451; };
+template <> struct InvSqrtC<5> { static constexpr double v = 0.44721359549995793928; };
+template <> struct InvSqrtC<7> { static constexpr double v = 0.37796447300922722721; };
+
 template <> struct Spin<1> {
     static constexpr int C = 3;
     __device__ static constexpr double lad(int i) { return 1.4142135623730950488; }
@@ -456,7 +464,7 @@ struct Dens {
         }
         A00 = mk<T2>(0, 0);
         if (F >= 2) {
-            const T sg = T(1.0 / sqrt(double(C)));
+            const T sg = T(InvSqrtC<C>::v);
 #pragma unroll
             for (int i = 0; i < F; ++i) caxpy(A00, T((i & 1) ? -2.0 : 2.0) * sg, cmul(x[i], x[C - 1 - i]));
             caxpy(A00, T((F & 1) ? -1.0 : 1.0) * sg, cmul(x[F], x[F]));
@@ -512,7 +520,7 @@ __device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<
         if (k + 1 < C) cfma(r, cscale(Fm, T(0.5) * g1 * T(Spin<F>::lad(k))), x[k + 1]);
         if (k >= 1) cfma(r, cscale(D.Fp, T(0.5) * g1 * T(Spin<F>::lad(k - 1))), x[k - 1]);
         if (F >= 2) {
-            const T sg = T((k & 1) ? -1.0 : 1.0) * T(1.0 / sqrt(double(C)));
+            const T sg = T((k & 1) ? -1.0 : 1.0) * T(InvSqrtC<C>::v);
             cfma(r, cscale(D.A00, g2 * sg), cconj(x[C - 1 - k]));
         }
         if (F == 3) {
@@ -554,7 +562,7 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
     }
     T2 dA00 = mk<T2>(0, 0);
     if (F >= 2) {
-        const T sg = T(1.0 / sqrt(double(C)));
+        const T sg = T(InvSqrtC<C>::v);
 #pragma unroll
         for (int i = 0; i < C; ++i) caxpy(dA00, T((i & 1) ? -2.0 : 2.0) * sg, cmul(z[i], x[C - 1 - i]));
     }
@@ -590,7 +598,7 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
             cfma(r, cscale(dFp, c), x[k - 1]);
         }
         if (F >= 2) {
-            const T sg = T((k & 1) ? -1.0 : 1.0) * T(1.0 / sqrt(double(C))) * g2;
+            const T sg = T((k & 1) ? -1.0 : 1.0) * T(InvSqrtC<C>::v) * g2;
             cfma(r, cscale(D.A00, sg), cconj(z[C - 1 - k]));
             cfma(r, cscale(dA00, sg), cconj(x[C - 1 - k]));
         }

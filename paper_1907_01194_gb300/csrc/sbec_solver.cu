@@ -11,7 +11,8 @@
 // Readings where the paper defers to the cited ARNT paper or is silent:
 //  * RGBB: first step gamma_0 = 1e-3; BB step |<s,v>|/<v,v> clamped to
 //    [1e-10, 1e10]; rho = 1e-4, varrho = 0.85, delta = 0.2; at most 10
-//    reductions, after which the last trial is taken.
+//    reductions, after which the last trial is taken; a trial whose energy is
+//    within the rounding floor (below) of the current one passes the test.
 //  * ARNT: eta1 = 0.01, eta2 = 0.9, gamma0 = 0.2, gamma1 = 1, gamma2 = 10,
 //    sigma_k = sigma_hat_k ||grad||, sigma_hat_0 = 1 (Sec. 7.1); after negative
 //    curvature sigma_{k+1} = max(sigma_{k+1}, sigma_est) (gamma_tilde = 0).
@@ -283,13 +284,14 @@ struct Solver {
                 gam = fmin(fmax(gam, 1e-10), 1e10);
             }
             const double slope = -gn * gn;
+            const double noise = 100.0 * (sizeof(T) == 8 ? kEps : 1.1920928955078125e-07) * fmax(1.0, fabs(E));
             double t = gam, Ez = INFINITY;
             for (int bt = 0; bt <= 10; ++bt) {
                 TRY(retract(u, rg, -t, z));
                 TRY(energy(z));
                 PULL(ds);
                 Ez = (ds == SBEC_ERR_DOMAIN) ? INFINITY : sc(SBEC_S_ENERGY);
-                if (Ez <= Ck + 1e-4 * t * slope) break;
+                if (Ez <= Ck + 1e-4 * t * slope || fabs(Ez - E) <= noise) break;
                 t *= 0.2;
             }
             if (!isfinite(Ez)) return SBEC_ERR_DOMAIN;
@@ -566,7 +568,9 @@ struct BatchSolver {
                 for (int b = 0; b < B; ++b) {
                     if (!tr[b]) continue;
                     Ez[b] = dstat[b] == SBEC_ERR_DOMAIN ? INFINITY : hs(b)[SBEC_S_ENERGY];
-                    if (Ez[b] <= Ck[b] + 1e-4 * t[b] * slope[b]) tr[b] = 0;
+                    const double noise = 100.0 * (sizeof(T) == 8 ? kEps : 1.1920928955078125e-07) *
+                                         fmax(1.0, fabs(E[b]));
+                    if (Ez[b] <= Ck[b] + 1e-4 * t[b] * slope[b] || fabs(Ez[b] - E[b]) <= noise) tr[b] = 0;
                     else if (bt < 10) t[b] *= 0.2;
                     more = more || tr[b];
                 }
