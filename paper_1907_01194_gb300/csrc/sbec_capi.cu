@@ -112,6 +112,8 @@ void free_handle(sbec_handle* h) {
     cudaFree(h->work.scal);
     cudaFree(h->d_ppb);
     cudaFree(h->d_Mb);
+    cudaFree(h->d_imap);
+    if (h->h_imap) cudaFreeHost(h->h_imap);
     for (int i = 0; i < 3; ++i) cudaFree(h->stage[i]);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     if (h->prof.ev) {
@@ -180,6 +182,8 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     sbec::Geom& g = h->geom;
     g.F = P.F; g.C = 2 * P.F + 1; g.dim = P.dim;
     g.B = B;
+    g.nl = B;          // launches cover the whole batch unless a solve narrows them
+    g.imap = nullptr;
     double dV = 1.0;
     for (int ax = 0; ax < 3; ++ax) {
         g.n[ax] = P.n[ax];
@@ -231,7 +235,9 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     ok = ok && cudaMallocHost((void**)&h->h_scal, nscal * sizeof(double)) == cudaSuccess;
     if (ok && B > 1) {
         ok = cudaMalloc(&h->d_ppb, (size_t)B * sizeof(sbec::PointParams)) == cudaSuccess &&
-             cudaMalloc((void**)&h->d_Mb, (size_t)B * sizeof(double)) == cudaSuccess;
+             cudaMalloc((void**)&h->d_Mb, (size_t)B * sizeof(double)) == cudaSuccess &&
+             cudaMalloc((void**)&h->d_imap, (size_t)B * sizeof(int)) == cudaSuccess &&
+             cudaMallocHost((void**)&h->h_imap, (size_t)B * sizeof(int)) == cudaSuccess;
     }
     if (!ok) { cudaGetLastError(); free_handle(h); return SBEC_ERR_CUDA; }
 

@@ -25,6 +25,8 @@ struct sbec_handle {
     int B;                // instances of a batch handle (1 for sbec_create)
     void* d_ppb;          // per-instance PointParams (batch handles)
     double* d_Mb;         // per-instance magnetisations (batch handles)
+    int* d_imap;          // launch slot -> instance map of a batch solve (B ints, device)
+    int* h_imap;          // its pinned host mirror
 };
 
 // helpers of the C-ABI translation unit used by the solver

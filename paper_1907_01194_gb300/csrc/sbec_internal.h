@@ -58,6 +58,10 @@ struct Geom {
     const void* ppb;          // PointParams[B]
     const double* Mb;         // M[B]
     const double* skip;       // the handle's scalar blocks: S_SKIP != 0 switches an instance off
+    // instances a launch covers: nl of them, listed in imap (device, launch slot ->
+    // instance), or all B when imap is null (nl = B)
+    int nl;
+    const int* imap;
     Tune tune;
 };
 

@@ -25,6 +25,13 @@ __device__ __forceinline__ bool skipped(const double* scal0, long long inst) {
     return scal0 != nullptr && scal0[inst * S_COUNT + S_SKIP] != 0.0;
 }
 
+// Launch slot -> instance of a batch: a launch covers the nl instances listed in
+// imap (the running ones of a lock-step solve), or all of them when imap is null.
+// Partial sums are laid out by slot, data and scalar blocks by instance.
+__device__ __forceinline__ long long inst_of(const int* imap, long long slot) {
+    return imap ? (long long)imap[slot] : slot;
+}
+
 #define SBEC_CUDA_TRY(expr)                                   \
     do {                                                      \
         cudaError_t e_ = (expr);                              \
@@ -75,6 +82,7 @@ struct XArgs {
     long long rpi;              // grid rows (x lines) per instance
     const PointParams* ppb;     // per-instance point parameters (batches) or null
     const double* skip;         // scalar blocks (S_SKIP flags) or null
+    const int* imap;            // launch slot -> instance, or null (identity)
 };
 
 // Shift of the Hessian epilogue per component: sigma (times the instance's
@@ -102,8 +110,9 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
     const int tid = threadIdx.x, nth = blockDim.x;
     // instance of this block (blocks never straddle instances) and its offsets
     const long long growrow = (long long)blockIdx.x * RPB;
-    const long long inst = growrow / a.rpi;
-    const long long row0 = growrow - inst * a.rpi;
+    const long long slot = growrow / a.rpi;
+    const long long inst = inst_of(a.imap, slot);
+    const long long row0 = growrow - slot * a.rpi;
     const long long foff = inst * (long long)C * a.G;
     const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + foff;
     const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
@@ -252,6 +261,7 @@ struct SArgs {
     int nblk;
     int C;                // components (instance = pencil component / C)
     const double* skip;   // scalar blocks (S_SKIP flags) or null
+    const int* imap;      // launch slot -> instance, or null (identity)
 };
 
 template <typename T, int MODE, int ITEMS>
@@ -264,8 +274,10 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
     long long b = blockIdx.x;
     const int xt = (int)(b % a.ntx); b /= a.ntx;
     const int o = (int)(b % a.nouter);
-    const int c = (int)(b / a.nouter);
-    if (skipped(a.skip, c / a.C)) return;
+    const int cs = (int)(b / a.nouter);                     // slot * C + component
+    const long long inst = inst_of(a.imap, cs / a.C);
+    const long long c = inst * a.C + (cs % a.C);
+    if (skipped(a.skip, inst)) return;
     const long long obase = (a.axis == 1) ? (long long)o * a.ny * a.nx : (long long)o * a.nx;
     const long long base = (long long)c * a.G + obase + (long long)xt * W;
     const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in);
@@ -339,8 +351,10 @@ __global__ void __launch_bounds__(256, 2) k_spass2(const SArgs a) {
     long long b = blockIdx.x;
     const int xt = (int)(b % a.ntx); b /= a.ntx;
     const int o = (int)(b % a.nouter);
-    const int c = (int)(b / a.nouter);
-    if (skipped(a.skip, c / a.C)) return;
+    const int cs = (int)(b / a.nouter);                     // slot * C + component
+    const long long inst = inst_of(a.imap, cs / a.C);
+    const long long c = inst * a.C + (cs % a.C);
+    if (skipped(a.skip, inst)) return;
     const long long obase = (a.axis == 1) ? (long long)o * a.ny * a.nx : (long long)o * a.nx;
     const long long base = (long long)c * a.G + obase + (long long)xt * W + w;
     const T2* __restrict__ src = reinterpret_cast<const T2*>(a.in) + base;
@@ -441,8 +455,9 @@ __global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
     const int p = tid / N1, q = tid & (N1 - 1);
     const bool on = p < P;
     const long long growrow = (long long)blockIdx.x * RPB;
-    const long long inst = growrow / a.rpi;
-    const long long row0 = growrow - inst * a.rpi;
+    const long long slot = growrow / a.rpi;
+    const long long inst = inst_of(a.imap, slot);
+    const long long row0 = growrow - slot * a.rpi;
     const long long foff = inst * (long long)C * a.G;
     if (skipped(a.skip, inst)) return;
     const int rg = p / C, cc = p - rg * C;
@@ -547,7 +562,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
     constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
     constexpr int NA = HESS ? 3 : 2;                  // staged arrays X, L X (, Z)
     constexpr int P = kEpiThreads;
-    const long long inst = blockIdx.y;
+    const long long inst = inst_of(a.imap, blockIdx.y);
     const long long foff = inst * (long long)C * G;
     const T2* __restrict__ LX = reinterpret_cast<const T2*>(lxp) + foff;
     const T2* __restrict__ Xp = reinterpret_cast<const T2*>(a.X) + foff;
@@ -633,11 +648,12 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
 // partials: n_l = |u_l|^2 (q = l index), t_l = <u_l, w_l> (q = C + l)
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials,
-                                                    const double* skip) {
+                                                    const double* skip, const int* imap) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    if (skipped(skip, blockIdx.y)) return;
-    const long long foff = (long long)blockIdx.y * C * G;
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(skip, inst)) return;
+    const long long foff = inst * C * G;
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
     Acc<T> acc[2 * C];
@@ -658,12 +674,13 @@ __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* 
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* Wp, void* Op, long long G,
                                                     const double* __restrict__ scal0, int ia, int ib,
-                                                    double* partials) {
+                                                    double* partials, const int* imap) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    if (skipped(scal0, blockIdx.y)) return;
-    const long long foff = (long long)blockIdx.y * C * G;
-    const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long foff = inst * C * G;
+    const double* scal = scal0 + inst * S_COUNT;
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Wv = reinterpret_cast<const T2*>(Wp) + foff;
     T2* __restrict__ O = Op ? reinterpret_cast<T2*>(Op) + foff : nullptr;
@@ -689,12 +706,14 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
 // w = U + t Xi into out; partials m_l = |w_l|^2
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
-                                                   double* partials, const double* __restrict__ scal0, int tslot) {
+                                                   double* partials, const double* __restrict__ scal0, int tslot,
+                                                   const int* imap) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    if (skipped(scal0, blockIdx.y)) return;
-    const long long foff = (long long)blockIdx.y * C * G;
-    if (tslot >= 0) t *= scal0[(size_t)blockIdx.y * S_COUNT + tslot];
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long foff = inst * C * G;
+    if (tslot >= 0) t *= scal0[(size_t)inst * S_COUNT + tslot];
     const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
     const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
     T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
@@ -716,12 +735,14 @@ __global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* X
 
 // out_l *= scal[S_SIG + l]
 template <typename T, int F>
-__global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal0) {
+__global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const double* __restrict__ scal0,
+                                               const int* imap) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
-    if (skipped(scal0, blockIdx.y)) return;
-    const long long foff = (long long)blockIdx.y * C * G;
-    const double* scal = scal0 + (long long)blockIdx.y * S_COUNT;
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long foff = inst * C * G;
+    const double* scal = scal0 + inst * S_COUNT;
     T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
     T s[C];
 #pragma unroll
@@ -763,15 +784,16 @@ __device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int nto
 
 // energy: scal[E] = sum of partA quantities 0..nqa-1 (+ partB quantity 0)
 static __global__ void k_fin_energy(const double* pa, int na_tot, int na_inst, int nqa, const double* pb, int nb_tot,
-                                    int nb_inst, double* scal0) {
+                                    int nb_inst, double* scal0, const int* imap) {
     __shared__ double va[4], vb[1];
     const int b = blockIdx.x;
-    if (skipped(scal0, b)) return;
+    const long long inst = inst_of(imap, b);
+    if (skipped(scal0, inst)) return;
     const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
     warp_sums(pa, na_tot, b * na_inst, na_inst, qa, nqa, va);
     if (pb) warp_sums(pb, nb_tot, b * nb_inst, nb_inst, qb, 1, vb);
     if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)b * S_COUNT;
+        double* scal = scal0 + (size_t)inst * S_COUNT;
         double e = 0.0;
         for (int q = 0; q < nqa; ++q) e += va[q];
         if (pb) e += vb[0];
@@ -784,10 +806,12 @@ static __global__ void k_fin_energy(const double* pa, int na_tot, int na_inst, i
 // t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
 // beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
 static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int F, int qe, int qn, int qt, double M0,
-                                  const double* Mb, double* scal0, int slot_a, int slot_b, int write_grad_info) {
+                                  const double* Mb, double* scal0, int slot_a, int slot_b, int write_grad_info,
+                                  const int* imap) {
     const int C = 2 * F + 1;
     const int b = blockIdx.x;
-    if (skipped(scal0, b)) return;
+    const long long inst = inst_of(imap, b);
+    if (skipped(scal0, inst)) return;
     __shared__ double v[15];
     int qs[15];
     int nq = 0;
@@ -796,8 +820,8 @@ static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int
     if (qe >= 0) qs[nq++] = qe;
     warp_sums(pa, na_tot, b * na_inst, na_inst, qs, nq, v);
     if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)b * S_COUNT;
-        const double M = Mb ? Mb[b] : M0;
+        double* scal = scal0 + (size_t)inst * S_COUNT;
+        const double M = Mb ? Mb[inst] : M0;
         double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, bb = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
         for (int i = 0; i < C; ++i) {
             const double l = double(F - i), nl = v[i], tl = v[C + i];
@@ -821,13 +845,15 @@ static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int
     }
 }
 
-static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, double* scal0, int slot) {
-    if (skipped(scal0, blockIdx.x)) return;
+static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, double* scal0, int slot,
+                                  const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.x);
+    if (skipped(scal0, inst)) return;
     __shared__ double v[1];
     const int q[1] = {0};
     warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, q, 1, v);
     if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
+        double* scal = scal0 + (size_t)inst * S_COUNT;
         scal[slot] = v[0];
         if (!isfinite(v[0])) set_status(scal, SBEC_ERR_NONFINITE);
     }
@@ -852,16 +878,17 @@ __device__ __forceinline__ double warp_sum_bcast(double v) {
 }
 
 static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst, int F, double M0, const double* Mb,
-                                       int kind, double* scal0) {
-    if (skipped(scal0, blockIdx.x)) return;
+                                       int kind, double* scal0, const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.x);
+    if (skipped(scal0, inst)) return;
     __shared__ double m[7];
     const int C = 2 * F + 1;
     const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
     warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, C, m);
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
-    double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
-    const double M = Mb ? Mb[blockIdx.x] : M0;
+    double* scal = scal0 + (size_t)inst * S_COUNT;
+    const double M = Mb ? Mb[inst] : M0;
     // f2 = largest l with w_l != 0 (component index i1), f1 = smallest (index i2)
     int i1 = -1, i2 = -1;
     for (int i = 0; i < C; ++i)
@@ -960,12 +987,13 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const double* __restrict__ scal0,
-                                                 double* partials) {
+                                                 double* partials, const int* imap) {
     // out may alias A, B, D1 or D2 (same index only), so no __restrict__ here;
-    // blockIdx.y is the instance, N the reals per instance
-    const long long off = (long long)blockIdx.y * N;
-    const double* scal = scal0 + (size_t)blockIdx.y * S_COUNT;
-    if (skipped(scal0, blockIdx.y)) return;
+    // blockIdx.y is the launch slot of the instance, N the reals per instance
+    const long long inst = inst_of(imap, blockIdx.y);
+    const long long off = inst * N;
+    const double* scal = scal0 + (size_t)inst * S_COUNT;
+    if (skipped(scal0, inst)) return;
     const T* A = reinterpret_cast<const T*>(L.A) + off;
     const T* B = L.B ? reinterpret_cast<const T*>(L.B) + off : nullptr;
     const T* D1 = L.D1 ? reinterpret_cast<const T*>(L.D1) + off : nullptr;
@@ -1000,9 +1028,10 @@ __global__ void __launch_bounds__(256) k_lincomb(const Lin L, long long N, const
 // partials q0 = <A, B>, q1 = <C, D> (C null: skip)
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, const void* Cp, const void* Dp,
-                                              long long N, double* partials, const double* skip) {
-    if (skipped(skip, blockIdx.y)) return;
-    const long long off = (long long)blockIdx.y * N;
+                                              long long N, double* partials, const double* skip, const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(skip, inst)) return;
+    const long long off = inst * N;
     const T* __restrict__ A = reinterpret_cast<const T*>(Ap) + off;
     const T* __restrict__ B = reinterpret_cast<const T*>(Bp) + off;
     const T* __restrict__ Cv = Cp ? reinterpret_cast<const T*>(Cp) + off : nullptr;
@@ -1020,9 +1049,10 @@ __global__ void __launch_bounds__(256) k_dot2(const void* Ap, const void* Bp, co
 // partials q0 = <u - up, g - gp>, q1 = |g - gp|^2 (the BB quantities s^T v, v^T v)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp, const void* Gp, const void* GPp,
-                                                long long N, double* partials, const double* skip) {
-    if (skipped(skip, blockIdx.y)) return;
-    const long long off = (long long)blockIdx.y * N;
+                                                long long N, double* partials, const double* skip, const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(skip, inst)) return;
+    const long long off = inst * N;
     const T* __restrict__ U = reinterpret_cast<const T*>(Up) + off;
     const T* __restrict__ UP = reinterpret_cast<const T*>(UPp) + off;
     const T* __restrict__ G = reinterpret_cast<const T*>(Gp) + off;
@@ -1040,13 +1070,15 @@ __global__ void __launch_bounds__(256) k_bbdots(const void* Up, const void* UPp,
 }
 
 // scal[slot + q] = sum of partial quantity q, q = 0..nq-1 (nq <= 2), per instance
-static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int nq, double* scal0, int slot) {
-    if (skipped(scal0, blockIdx.x)) return;
+static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int nq, double* scal0, int slot,
+                                  const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.x);
+    if (skipped(scal0, inst)) return;
     __shared__ double v[2];
     const int qs[2] = {0, 1};
     warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, nq, v);
     if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
+        double* scal = scal0 + (size_t)inst * S_COUNT;
         for (int q = 0; q < nq; ++q) {
             scal[slot + q] = v[q];
             if (!isfinite(v[q])) set_status(scal, SBEC_ERR_NONFINITE);
@@ -1057,9 +1089,10 @@ static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int
 // scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha), per
 // instance; scal[dst + 1] is the guard flag of the guarded updates
 static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
-                               int mask) {
-    if (threadIdx.x != 0 || skipped(scal0, blockIdx.x)) return;
-    double* scal = scal0 + (size_t)blockIdx.x * S_COUNT;
+                               int mask, const int* imap) {
+    const long long inst = inst_of(imap, blockIdx.x);
+    if (threadIdx.x != 0 || skipped(scal0, inst)) return;
+    double* scal = scal0 + (size_t)inst * S_COUNT;
     bool ok = (mask < 0) || (scal[mask] != 0.0);
     if (guard_kap >= 0) ok = ok && scal[guard_kap] > eps * scal[guard_pp];
     scal[dst] = ok ? scal[num] / scal[den] : 0.0;
@@ -1176,7 +1209,7 @@ static XCfg xcfg(const Geom& g) {
         c.two = 1; c.logn = lg; c.rpb = rpb; c.items = 0;
         c.nth = ((rpb * g.C * N1 + 31) / 32) * 32;
         c.nblk_inst = (int)(rows_inst / rpb);
-        c.nblk = c.nblk_inst * g.B;
+        c.nblk = c.nblk_inst * g.nl;
         c.smem = (size_t)rpb * g.C * N2 * (N1 + 1) * sizeof(typename C2<T>::t);
         return c;
     }
@@ -1198,7 +1231,7 @@ static XCfg xcfg(const Geom& g) {
     c.two = 0; c.logn = g.logn[0];
     c.rpb = rpb; c.nth = nth; c.items = it2;
     c.nblk_inst = (int)(rows_inst / rpb);
-    c.nblk = c.nblk_inst * g.B;
+    c.nblk = c.nblk_inst * g.nl;
     c.smem = xsmem<T>(P, n);
     return c;
 }
@@ -1227,7 +1260,7 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
             SCfg c;
             c.two = 1; c.logn = lg; c.W = W; c.nth = W * N1; c.items = 0;
             c.nblk_inst = (int)((long long)g.C * outer * (nx / W));
-            c.nblk = c.nblk_inst * g.B;
+            c.nblk = c.nblk_inst * g.nl;
             c.smem = (size_t)N2 * (N1 * W + (W < 16 ? W : 0)) * sizeof(T2);
             return c;
         }
@@ -1244,12 +1277,14 @@ static SCfg scfg(const Geom& g, int axis, int num_sms) {
     c.two = 0; c.logn = lg;
     c.W = W; c.nth = nth; c.items = it2;
     c.nblk_inst = (int)((long long)g.C * outer * (nx / W));
-    c.nblk = c.nblk_inst * g.B;
+    c.nblk = c.nblk_inst * g.nl;
     c.smem = (size_t)W * n * sizeof(T2);
     return c;
 }
 
-// blocks per instance of the grid-stride elementwise kernels
+// blocks per instance of the grid-stride elementwise kernels (from the batch size B,
+// not from the number of instances a launch covers, so that every instance's
+// partial sums have the same order whichever instances run alongside it)
 static int elem_blocks(long long G, int num_sms, int B = 1, int per_sm = 0) {
     long long b = (G + 255) / 256;
     long long cap = (long long)(per_sm > 0 ? per_sm : 8) * num_sms / (B > 0 ? B : 1);
@@ -1408,7 +1443,7 @@ static int launch_epi(const Geom& g, const Work& w, const XArgs& a, int ne, cuda
     static size_t granted = 0;
     if (int st = ensure_smem(kern, smem, granted)) return st;
     ProfScope ps(w.prof, HESS ? K_X_INV_HESS : K_X_INV_GRAD, s);
-    kern<<<dim3(ne, g.B), kEpiThreads, smem, s>>>(a, w.work, g.G);
+    kern<<<dim3(ne, g.nl), kEpiThreads, smem, s>>>(a, w.work, g.G);
     SBEC_LAUNCH_CHECK();
     return SBEC_OK;
 }
@@ -1427,6 +1462,7 @@ static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void*
     a.partials = part; a.nblk = c.nblk;
     a.C = g.C;
     a.skip = g.skip;
+    a.imap = g.imap;
     return a;
 }
 
@@ -1441,6 +1477,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.rpi = g.G / g.n[0];
     a.ppb = reinterpret_cast<const PointParams*>(g.ppb);
     a.skip = g.skip;
+    a.imap = g.imap;
     return a;
 }
 
@@ -1490,8 +1527,8 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
             a.X = X;
             st = launch_epi<T, F, false>(g, w, a, ne, s);
             if (st) return st;
-            SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                        SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+            SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                        SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
             goto rgrad;
         }
         XArgs a = xargs<T>(g, c, w.work, gout, w.partA);
@@ -1499,14 +1536,14 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         st = launch_x<T, F, X_INV_GRAD>(c, a, w, s);
         if (st) return st;
     }
-    SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
+    SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
 rgrad:
     if (Griem || want_norm) {
         const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
-                    SBEC_S_BETA_G, w.partB);
-        SBEC_LAUNCH(K_FIN, k_fin_norm, g.B, 256, w.partB, nb * g.B, nb, w.scal, SBEC_S_RGRAD_NORM2);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
+                    SBEC_S_BETA_G, w.partB, g.imap);
+        SBEC_LAUNCH(K_FIN, k_fin_norm, g.nl, 256, w.partB, nb * g.nl, nb, w.scal, SBEC_S_RGRAD_NORM2, g.imap);
     }
     return SBEC_OK;
 }
@@ -1518,7 +1555,7 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
     if (g.dim == 1) {
         st = launch_x<T, F, X_FULL_ENERGY>(c, xargs<T>(g, c, X, nullptr, w.partA), w, s);
         if (st) return st;
-        SBEC_LAUNCH(K_FIN, k_fin_energy, g.B, 256, w.partA, c.nblk, c.nblk_inst, 2, nullptr, 0, 0, w.scal);
+        SBEC_LAUNCH(K_FIN, k_fin_energy, g.nl, 256, w.partA, c.nblk, c.nblk_inst, 2, nullptr, 0, 0, w.scal, g.imap);
         return SBEC_OK;
     }
     st = launch_x<T, F, X_FWD_EPW>(c, xargs<T>(g, c, X, w.work, w.partA), w, s);
@@ -1535,8 +1572,8 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
         st = launch_s<T, S_PARSEVAL>(cl, sargs<T>(g, cl, 2, w.work, nullptr, w.partB), w, s);
     }
     if (st) return st;
-    SBEC_LAUNCH(K_FIN, k_fin_energy, g.B, 256, w.partA, c.nblk, c.nblk_inst, 1, w.partB, cl.nblk, cl.nblk_inst,
-                w.scal);
+    SBEC_LAUNCH(K_FIN, k_fin_energy, g.nl, 256, w.partA, c.nblk, c.nblk_inst, 1, w.partB, cl.nblk, cl.nblk_inst,
+                w.scal, g.imap);
     return SBEC_OK;
 }
 
@@ -1548,11 +1585,11 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
     const void* zin = Z;
     if (riem) {
         // xi = P_u Z (Lemma 4.1)
-        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.B), 256, X, Z, g.G, w.partB, w.scal);
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partB, nb * g.B, nb, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA, S_PB,
-                    0);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB,
-                    w.partB);
+        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.nl), 256, X, Z, g.G, w.partB, w.scal, g.imap);
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partB, nb * g.nl, nb, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA, S_PB,
+                    0, g.imap);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB,
+                    w.partB, g.imap);
         zin = w.work2;
     }
     const XCfg c = xcfg<T>(g);
@@ -1578,10 +1615,10 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
             st = launch_epi<T, F, true>(g, w, a, ne, s);
             if (st) return st;
             if (riem) {
-                SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, ne * g.B, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
-                            S_PA, S_PB, 0);
-                SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
-                            w.partB);
+                SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
+                            S_PA, S_PB, 0, g.imap);
+                SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
+                            w.partB, g.imap);
             }
             return SBEC_OK;
         }
@@ -1589,9 +1626,9 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (st) return st;
     }
     if (riem) {
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.B, 256, w.partA, c.nblk, c.nblk_inst, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA,
-                    S_PB, 0);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.B), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB);
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA,
+                    S_PB, 0, g.imap);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB, g.imap);
     }
     return SBEC_OK;
 }
@@ -1600,9 +1637,9 @@ template <typename T, int F>
 static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
                      cudaStream_t s, int tslot = -1) {
     const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.B), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot);
-    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.B, 256, w.partB, nb * g.B, nb, F, g.M, g.Mb, kind, w.scal);
-    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.B), 256, out, g.G, w.scal);
+    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.nl), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot, g.imap);
+    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.nl, 256, w.partB, nb * g.nl, nb, F, g.M, g.Mb, kind, w.scal, g.imap);
+    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.nl), 256, out, g.G, w.scal, g.imap);
     return SBEC_OK;
 }
 
@@ -1650,8 +1687,8 @@ int Ops<T>::lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cu
     const long long N = 2LL * g.C * g.G;
     const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
     const bool dots = (L.D1 || L.D2);
-    SBEC_LAUNCH(K_LIN, k_lincomb<T>, dim3(nb, g.B), 256, L, N, w.scal, dots ? w.partB : nullptr);
-    if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, dot_slot);
+    SBEC_LAUNCH(K_LIN, k_lincomb<T>, dim3(nb, g.nl), 256, L, N, w.scal, dots ? w.partB : nullptr, g.imap);
+    if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, 2, w.scal, dot_slot, g.imap);
     return SBEC_OK;
 }
 
@@ -1660,8 +1697,8 @@ int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, con
                  cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
     const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
-    SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.B), 256, A, B, C, D, N, w.partB, w.scal);
-    SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, C ? 2 : 1, w.scal, slot);
+    SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.nl), 256, A, B, C, D, N, w.partB, w.scal, g.imap);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, C ? 2 : 1, w.scal, slot, g.imap);
     return SBEC_OK;
 }
 
@@ -1670,15 +1707,15 @@ int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, 
                    int slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
     const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
-    SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.B), 256, U, UP, Gv, GP, N, w.partB, w.scal);
-    SBEC_LAUNCH(K_FIN, k_fin_sums, g.B, 256, w.partB, nb * g.B, nb, 2, w.scal, slot);
+    SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.nl), 256, U, UP, Gv, GP, N, w.partB, w.scal, g.imap);
+    SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, 2, w.scal, slot, g.imap);
     return SBEC_OK;
 }
 
 template <typename T>
 int Ops<T>::ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
                   cudaStream_t s, int mask) {
-    SBEC_LAUNCH(K_FIN, k_ratio, g.B, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps, mask);
+    SBEC_LAUNCH(K_FIN, k_ratio, g.nl, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps, mask, g.imap);
     return SBEC_OK;
 }
 

@@ -91,6 +91,8 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
     sbec::Geom g = {};
     g.F = P.F; g.C = 2 * P.F + 1; g.dim = P.dim;
     g.B = 1;
+    g.nl = 1;
+    g.imap = nullptr;
     double dV = 1.0;
     for (int ax = 0; ax < 3; ++ax) {
         g.n[ax] = P.n[ax];

@@ -4,7 +4,8 @@
 // search, ratio test and sigma update).  Every vector operation runs on the
 // device.  The modified CG runs in chunks of cg_chunk iterations whose
 // coefficients and stopping tests are computed on the device (k_cg_ctl), each
-// chunk the replay of a CUDA graph; the host reads the scalar block once per
+// chunk the replay of a CUDA graph (one per state array, slot parity and set of
+// launched instances); the host reads the scalar block once per
 // chunk, line-search trial or outer iteration and keeps the rest of the control
 // flow.
 //
@@ -76,10 +77,10 @@ constexpr double kSkipCg = 2.0;
 // takes), on ||r|| <= the threshold or at the iteration cap; otherwise writes
 // beta = <r',r'>/<r,r> for the update p = r' + beta p.  An instance that ends
 // sets S_SKIP so that the rest of its chunk leaves its arrays and scalars alone.
-__global__ void k_cg_ctl(double* scal0, int B, int rr_now, int rr_next) {
+__global__ void k_cg_ctl(double* scal0, int nl, const int* imap, int rr_now, int rr_next) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    double* sc = scal0 + (size_t)b * sbec::S_COUNT;
+    if (b >= nl) return;
+    double* sc = scal0 + (size_t)(imap ? imap[b] : b) * sbec::S_COUNT;
     if (sc[sbec::S_SKIP] != 0.0) return;
     const double kap = sc[SL_KAP], pp = sc[SL_KAP + 1], rrn = sc[rr_next];
     const double j = sc[SL_J] + 1.0;
@@ -108,7 +109,10 @@ __global__ void k_unskip(double* scal0, int B) {
     if (b < B) scal0[(size_t)b * sbec::S_COUNT + sbec::S_SKIP] = 0.0;
 }
 
+// after a solve: every instance on again, launches over the whole batch
 int clear_skip(sbec_handle* h) {
+    h->geom.nl = h->B;
+    h->geom.imap = nullptr;
     k_unskip<<<(h->B + 127) / 128, 128, 0, h->stream>>>(h->work.scal, h->B);
     return cudaGetLastError() == cudaSuccess ? SBEC_OK : SBEC_ERR_CUDA;
 }
@@ -127,7 +131,7 @@ struct CgChunks {
     int K;
     bool graphs;
     cudaStream_t cap = nullptr;
-    struct Entry { const void* u; int par; cudaGraphExec_t exec; long long nodes; };
+    struct Entry { const void* u; int par; int nl; const int* imap; cudaGraphExec_t exec; long long nodes; };
     std::vector<Entry> cache;
 
     CgChunks(sbec_handle* hh, int k, bool gr)
@@ -157,7 +161,7 @@ struct CgChunks {
             if (e) return e;
             {
                 sbec::ProfScope ps(w.prof, sbec::K_FIN, cs);
-                k_cg_ctl<<<(g.B + 127) / 128, 128, 0, cs>>>(w.scal, g.B, rr_now, rr_next);
+                k_cg_ctl<<<(g.nl + 127) / 128, 128, 0, cs>>>(w.scal, g.nl, g.imap, rr_now, rr_next);
                 if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
             }
             e = lin(cs, p, r, 1.0, p, SL_BETA, -1, nullptr, SL_D0);
@@ -171,7 +175,7 @@ struct CgChunks {
         if (!graphs) return launch(h->stream, u, p, Hp, x, r, par0);
         const Entry* hit = nullptr;
         for (const auto& e : cache)
-            if (e.u == u && e.par == par0) hit = &e;
+            if (e.u == u && e.par == par0 && e.nl == g.nl && e.imap == g.imap) hit = &e;
         if (!hit) {
             if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return SBEC_ERR_CUDA;
             sbec::Prof* pr = w.prof;
@@ -183,7 +187,7 @@ struct CgChunks {
             const int e = launch(cap, u, p, Hp, x, r, par0);
             cudaGraph_t graph = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-            Entry ent{u, par0, nullptr, pr ? pr->launches - before : 0};
+            Entry ent{u, par0, g.nl, g.imap, nullptr, pr ? pr->launches - before : 0};
             if (pr) pr->launches = before;       // captured, not launched
             if (e || ce != cudaSuccess || !graph) {
                 if (graph) cudaGraphDestroy(graph);
@@ -489,11 +493,26 @@ struct BatchSolver {
         }
         return any ? push() : SBEC_OK;
     }
-    // host-written parameter slots back to the device (the block is in sync after pull)
+    // host-written parameter slots back to the device (the block is in sync after
+    // pull), and the launches narrowed to the instances runset() left running: the
+    // next kernels cover only those (slot -> instance map), so instances outside the
+    // phase cost no blocks at all
     int push() {
         const size_t n = (size_t)B * sbec::S_COUNT;
         if (cudaMemcpyAsync(w.scal, h->h_scal, n * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return SBEC_ERR_CUDA;
+        int nl = 0;
+        for (int b = 0; b < B; ++b)
+            if (hs(b)[sbec::S_SKIP] == 0.0) h->h_imap[nl++] = b;
+        if (nl == 0 || nl == B) {
+            h->geom.nl = B;
+            h->geom.imap = nullptr;
+            return SBEC_OK;
+        }
+        if (cudaMemcpyAsync(h->d_imap, h->h_imap, (size_t)nl * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+        h->geom.nl = nl;
+        h->geom.imap = h->d_imap;
         return SBEC_OK;
     }
 
@@ -654,10 +673,13 @@ struct BatchSolver {
                     TRY(cgc.run(u, p, Hp, x, r, (int)(done_its & 1)));
                     done_its += cgc.K;
                     TRY(pull());
-                    bool more = false;
-                    for (int b = 0; b < B; ++b) more = more || (cg[b] && hs(b)[SL_CG] != 0.0);
-                    if (!more) break;
+                    int still = 0;
+                    for (int b = 0; b < B; ++b) still += (cg[b] && hs(b)[SL_CG] != 0.0) ? 1 : 0;
+                    if (!still) break;
                     if (done_its >= cap_in) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+                    // once half of the launched instances have ended their CG, narrow the
+                    // launches to the others (a new chunk graph per launched set)
+                    if (2 * still <= h->geom.nl) TRY(push());
                 }
                 for (int b = 0; b < B; ++b) {
                     if (!cg[b]) continue;
