@@ -922,7 +922,14 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
                 }
                 const double h = warp_sum_bcast(th), dh = warp_sum_bcast(tdh);
                 if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
-                double rn = (dh > 0.0) ? r - h / dh : 0.5 * (lo + hi);
+                // a Newton step below 4 ulps of r ends the iteration (tested before the
+                // bracket, which a converged step may no longer clear)
+                const double dr = (dh > 0.0) ? h / dh : 0.0;
+                if (dh > 0.0 && fabs(dr) <= 4.0 * 2.220446049250313e-16 * fmax(fabs(r), 1e-300)) {
+                    r -= dr;
+                    break;
+                }
+                double rn = (dh > 0.0) ? r - dr : 0.5 * (lo + hi);
                 if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
                 const double step = fabs(rn - r);
                 r = rn;
@@ -954,6 +961,10 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
             for (int it = 0; it < 200 && ok; ++it) {
                 const double h = h3(r, &dh);
                 if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
+                if (dh > 0.0 && fabs(h / dh) <= 4.0 * 2.220446049250313e-16 * r) {
+                    r -= h / dh;
+                    break;
+                }
                 double rn = (dh > 0.0) ? r - h / dh : 0.5 * (lo + hi);
                 if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
                 const double step = fabs(rn - r);
