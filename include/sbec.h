@@ -104,8 +104,9 @@ int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* 
  * (Eq. 3.13).  riemannian != 0: HZ = Hess f(u)[xi] of Lemma 4.2 for
  * f = E + (sigma/2)||u - u_k||^2, i.e. P_u(nabla^2 E[xi] + sigma xi
  * - alpha_g xi - beta_g Gamma xi) with xi = P_u Z, using the alpha_g, beta_g
- * of the latest sbec_grad call at the same X (the call recomputes them when
- * X differs from that call's pointer). */
+ * of the latest sbec_grad call at the same X pointer, host or device (the call
+ * recomputes them when X differs from that call's pointer; after changing the
+ * contents of X in place, call sbec_grad again). */
 int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int riemannian,
                  void* HZ);
 

@@ -425,7 +425,7 @@ int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* 
              ? sbec::Ops<double>::grad(h->geom, h->work, Xd, ge, gr, rgrad_norm != nullptr, h->stream)
              : sbec::Ops<float>::grad(h->geom, h->work, Xd, ge, gr, rgrad_norm != nullptr, h->stream);
     if (st) return st;
-    h->last_grad_X = host ? nullptr : X;
+    h->last_grad_X = X;     // host or device: the caller's pointer identifies the state
     if ((st = copy_back(h, G_euc, ge))) return st;
     if ((st = copy_back(h, G_riem, gr))) return st;
     if (E || rgrad_norm || host) {
@@ -449,11 +449,11 @@ int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int
     if (st) return st;
     void* hz = stage_out_ptr(h, HZ, 2, &host);
     const bool dbl = h->prob.precision == SBEC_FP64;
-    if (riemannian && (host || h->last_grad_X != X)) {
+    if (riemannian && h->last_grad_X != X) {
         st = dbl ? sbec::Ops<double>::grad(h->geom, h->work, Xd, nullptr, nullptr, false, h->stream)
                  : sbec::Ops<float>::grad(h->geom, h->work, Xd, nullptr, nullptr, false, h->stream);
         if (st) return st;
-        h->last_grad_X = host ? nullptr : X;
+        h->last_grad_X = X;
     }
     st = dbl ? sbec::Ops<double>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream)
              : sbec::Ops<float>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream);

@@ -139,6 +139,30 @@ def test_host_pointers_match_device(dev):
     assert np.array_equal(Gd.cpu().numpy(), Gh)
 
 
+def test_host_riemannian_hessvec_uses_the_gradient_at_the_same_pointer(dev):
+    # the Lemma 4.2 coefficients come from the latest sbec_grad at the same X pointer,
+    # host or device; a new pointer recomputes them
+    sbec = _sbec()
+    w = CASES[2]
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    Z = torch.from_numpy(Zf).to(dev)
+    Hd = torch.empty_like(X)
+    Xh = np.array(Xf, copy=True)
+    Zh = np.array(Zf, copy=True)
+    Hh1, Hh2 = np.empty_like(Xf), np.empty_like(Xf)
+    with sbec.Handle.from_workload(w) as h:
+        h.grad(X)
+        h.hessvec(X, Z, Hd, sigma=0.2, riemannian=True)
+        h.sync()
+        h.grad(Xh)                                           # cached for the host pointer Xh
+        h.hessvec(Xh, Zh, Hh1, sigma=0.2, riemannian=True)
+        Xh2 = np.array(Xf, copy=True)                        # another pointer: recomputed
+        h.hessvec(Xh2, Zh, Hh2, sigma=0.2, riemannian=True)
+    assert np.array_equal(Hd.cpu().numpy(), Hh1)
+    assert np.array_equal(Hd.cpu().numpy(), Hh2)
+
+
 def test_deterministic_repeat(dev):
     sbec = _sbec()
     w = CASES[5]
