@@ -315,13 +315,14 @@ def energy(P: Problem, X):
     return float(E)
 
 
-def gradient(P: Problem, X):
-    """Euclidean gradient nabla E_h(X) w.r.t. Re<.,.>, Eq. (3.12) with h -> dV."""
+def _gradient_local(P: Problem, X, V):
+    """The terms of Eq. (3.12) other than L X, for rows X of the matrix (grid points)
+    with potential values V at those points: every one of them is pointwise."""
     b0, b1, b2, b3 = P.beta
     h = P.dV
-    V = P.V.reshape(P.G)[:, None]
+    V = np.asarray(V)[:, None]
     rho, Fa, A00, A2 = densities(P, X)
-    G = laplacian(P, X) + 2 * V * X + 2 * X * P.bvec[None, :]
+    G = 2 * V * X + 2 * X * P.bvec[None, :]
     G += (2 * b0 / h) * rho[:, None] * X
     for F, f in zip(Fa, (P.fx, P.fy, P.fz)):
         G += (2 * b1 / h) * F[:, None] * (X @ f.T)
@@ -332,13 +333,19 @@ def gradient(P: Problem, X):
     return G
 
 
-def hessvec(P: Problem, X, Z):
-    """Euclidean Hessian-vector product nabla^2 E_h(X)[Z], Eq. (3.13), h -> dV."""
+def gradient(P: Problem, X):
+    """Euclidean gradient nabla E_h(X) w.r.t. Re<.,.>, Eq. (3.12) with h -> dV."""
+    return laplacian(P, X) + _gradient_local(P, X, P.V.reshape(P.G))
+
+
+def _hessvec_local(P: Problem, X, Z, V):
+    """The terms of Eq. (3.13) other than L Z, for rows X, Z (grid points) with
+    potential values V there: every one of them is pointwise."""
     b0, b1, b2, b3 = P.beta
     h = P.dV
-    V = P.V.reshape(P.G)[:, None]
+    V = np.asarray(V)[:, None]
     rho, Fa, A00, A2 = densities(P, X)
-    H = laplacian(P, Z) + 2 * V * Z + 2 * Z * P.bvec[None, :]
+    H = 2 * V * Z + 2 * Z * P.bvec[None, :]
     reZX = np.sum(Z * X.conj(), axis=1).real                    # diag(Re(Z X^*))
     H += (2 * b0 / h) * (rho[:, None] * Z + 2 * reZX[:, None] * X)
     for F, f in zip(Fa, (P.fx, P.fy, P.fz)):
@@ -351,6 +358,45 @@ def hessvec(P: Problem, X, Z):
         ZAX = np.sum((Z @ Al) * X, axis=1)
         H += (2 * b3 / h) * (A2[l][:, None] * (Z.conj() @ Al) + 2 * ZAX[:, None] * (X.conj() @ Al))
     return H
+
+
+def hessvec(P: Problem, X, Z):
+    """Euclidean Hessian-vector product nabla^2 E_h(X)[Z], Eq. (3.13), h -> dV."""
+    return laplacian(P, Z) + _hessvec_local(P, X, Z, P.V.reshape(P.G))
+
+
+# ---------------------------------------------------------------------------
+# The same quantities at a few grid points of a large grid: L is the sum over
+# the axes of the 1D operator of Eq. (3.5) acting along that axis, so (L X)_j
+# needs one row of each 1D matrix and the grid lines through x_j.
+# ---------------------------------------------------------------------------
+
+def laplacian_at(P: Problem, X, idx):
+    """(L X)_j for the flat (C-order) grid indices idx."""
+    idx = np.asarray(idx)
+    Xg = np.asarray(X).reshape(P.shape + (P.C,))               # (n_z, n_y, n_x, C)
+    coords = np.unravel_index(idx, P.shape)                    # numpy axis order (z, y, x)
+    out = np.zeros((idx.size, P.C), dtype=complex)
+    for i in range(P.d):
+        ax = P.d - 1 - i                                       # numpy axis of problem axis i
+        L1 = dense_laplacian_1d(P.n[i], P.lo[i], P.hi[i])
+        for r in range(idx.size):
+            at = [int(coords[k][r]) for k in range(P.d)]
+            line = [slice(None) if k == ax else at[k] for k in range(P.d)]
+            out[r] += L1[at[ax], :] @ Xg[tuple(line)]
+    return out
+
+
+def gradient_at(P: Problem, X, idx):
+    """Rows idx of nabla E_h(X) (Eq. 3.12)."""
+    X = np.asarray(X)
+    return laplacian_at(P, X, idx) + _gradient_local(P, X[idx], P.V.reshape(P.G)[idx])
+
+
+def hessvec_at(P: Problem, X, Z, idx):
+    """Rows idx of nabla^2 E_h(X)[Z] (Eq. 3.13)."""
+    X, Z = np.asarray(X), np.asarray(Z)
+    return laplacian_at(P, Z, idx) + _hessvec_local(P, X[idx], Z[idx], P.V.reshape(P.G)[idx])
 
 
 def constraints(P: Problem, X):

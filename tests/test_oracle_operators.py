@@ -114,6 +114,33 @@ def test_laplacian_matches_dense_dft(n, lo, hi):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+def test_laplacian_at_matches_dense_rows():
+    # the point-sampled Laplacian against rows of the brute-force dense matrix
+    n, lo, hi = (8, 4, 16), (-2.0, -3.0, -1.0), (2.0, 1.0, 4.0)
+    G = int(np.prod(n))
+    P = O.Problem(F=1, n=n, lo=lo, hi=hi, beta=(0,), V=np.zeros(G))
+    X = crandn(G, 3)
+    idx = np.array([0, 5, 77, 130, G - 1, 311])
+    ref = (O.dense_laplacian(P) @ X)[idx]
+    got = O.laplacian_at(P, X, idx)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("F", [1, 2, 3])
+def test_gradient_and_hessvec_at_points_match_full(F):
+    # rows of the full Eq. (3.12)/(3.13) results (pinned by finite differences below)
+    n = (8, 4, 16)
+    G = int(np.prod(n))
+    P = O.Problem(F=F, n=n, lo=(-3.0, -2.0, -4.0), hi=(3.0, 2.0, 4.0), beta=(30.0, -2.0, 5.0, 1.5),
+                  V=rng.uniform(0, 3, G), p=0.3, q=0.2, M=0.1)
+    X = crandn(G, P.C) * 0.1
+    Z = crandn(G, P.C)
+    idx = np.array([3, 64, 100, 257, G - 2])
+    g, H = O.gradient(P, X), O.hessvec(P, X, Z)
+    assert np.max(np.abs(O.gradient_at(P, X, idx) - g[idx])) <= 1e-12 * np.max(np.abs(g))
+    assert np.max(np.abs(O.hessvec_at(P, X, Z, idx) - H[idx])) <= 1e-12 * np.max(np.abs(H))
+
+
 def test_laplacian_plane_wave_eigenvalue():
     # -d^2/dx^2 of e^{i lambda_p (x - a)} is lambda_p^2 exactly, the Nyquist mode included
     n, a, b = 16, -3.0, 5.0
