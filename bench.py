@@ -467,6 +467,9 @@ def run_ours(args, world, rank, local):
     tts = None
     if not args.no_solve and args.workload != "spin3_3d_256":
         tts = time_to_ground_state(args, sbec, torch, dev, stream, groups, w_main)
+    paper = None
+    if not args.no_solve and args.workload == "spin2_2d" and args.precision == "fp64":
+        paper = paper_case(args, sbec, torch, dev, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -496,7 +499,8 @@ def run_ours(args, world, rank, local):
                 "mixed_fp32_value": mixed_value,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
                 "time_to_ground_state_s": (tts or {}).get("fp64", {}).get("seconds"),
-                "time_to_ground_state": tts}
+                "time_to_ground_state": tts,
+                "paper_case": paper}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -588,6 +592,39 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
                               "converged": bool(sf["converged"])},
             "speedup_mixed_over_fp64": t64 / tmx if tmx > 0 else None,
             "energy_rel_diff": abs(sf["energy"] - s64["energy"]) / abs(s64["energy"])}
+
+
+# The paper's spin-2 2D case (Sec. 7.1, table of spin-2 results in 2D, ARNT with R1):
+# printed energy f and time in seconds (MATLAB R2018b on 12 Xeon E5-2680 v3 cores)
+PAPER_SPIN2_2D = {0.0: (14.3386, 8.3), 0.5: (14.3730, 13.5), 1.5: (14.6754, 13.5)}
+
+
+def paper_case(args, sbec, torch, dev, stream):
+    """Context: the paper's spin-2 2D solves (cascadic 64^2 -> 128^2 -> 256^2, R1, the
+    paper's tolerances 1e-5 / 1e-6 and nematic initial data) timed on this GPU next to
+    the paper's printed energies and CPU times."""
+    runs = []
+    for M, (e_printed, t_paper) in PAPER_SPIN2_2D.items():
+        ws = [W.paper_spin2_2d(M, n) for n in (64, 128, 256)]
+        hs = [sbec.Handle.from_workload(w, stream=stream.cuda_stream) for w in ws]
+        for h, w in zip(hs, ws):
+            if not args.no_autotune:
+                h.autotune(torch.from_numpy(W.paper_nematic_initial(w)).to(dev))
+        states = [torch.from_numpy(W.paper_nematic_initial(ws[0])).to(dev)] + [
+            torch.empty((5, n, n), dtype=torch.complex128, device=dev) for n in (128, 256)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sbec.solve_cascadic(hs, states, tol=1e-6, tol_coarse=1e-5)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        for h in hs:
+            h.close()
+        runs.append({"M": M, "seconds": dt, "energy": st["energy"], "grad_norm": st["grad_norm"],
+                     "paper_energy": e_printed, "paper_seconds": t_paper,
+                     "speedup_vs_paper": t_paper / dt if dt > 0 else None})
+    return {"case": "spin-2 2D, 256^2 x 5, beta = (243, 12.1, -13), [-8,8]^2 (paper Sec. 7.1)",
+            "paper_hardware": "MATLAB R2018b, 12 x Intel Xeon E5-2680 v3 (context, not the target)",
+            "runs": runs}
 
 
 def main():

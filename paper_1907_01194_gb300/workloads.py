@@ -161,6 +161,29 @@ def spin3_3d_256() -> Workload:
                     lattice_k=np.pi / 2, seed=SEED_BASE + 5)
 
 
+def paper_spin2_2d(M: float, n: int = 256) -> Workload:
+    """The paper's spin-2 2D case (Sec. 7.1): V = |x|^2/2 + 10 sum sin^2(pi x_i / 2),
+    beta = (243, 12.1, -13), box [-8,8]^2, n = 2^8 per axis on the finest mesh."""
+    return Workload(f"paper_spin2_2d_n{n}", F=2, n=(n, n), lo=(-8.0, -8.0), hi=(8.0, 8.0),
+                    beta=(243.0, 12.1, -13.0, 0.0), M=M, lattice_amp=10.0, lattice_k=np.pi / 2)
+
+
+def paper_nematic_initial(w: Workload) -> np.ndarray:
+    """The paper's initial data for nematic spin-2 interactions (Sec. 7):
+    U phi_0 with U = (sqrt(2+M)/2, 0, 0, 0, sqrt(2-M)/2) and
+    phi_0 = pi^{-d/4} exp(-|x|^2/2), scaled by sqrt(dV); complex128, (5,) + w.shape."""
+    assert w.F == 2
+    axes = grid_axes(w)
+    r2 = np.zeros(w.shape)
+    for i, x in enumerate(axes):
+        sh = [1] * w.dim
+        sh[w.dim - 1 - i] = w.n[i]
+        r2 = r2 + (x ** 2).reshape(sh)
+    phi0 = np.pi ** (-w.dim / 4.0) * np.exp(-r2 / 2.0)
+    U = np.array([np.sqrt(2.0 + w.M) / 2.0, 0.0, 0.0, 0.0, np.sqrt(2.0 - w.M) / 2.0])
+    return (np.sqrt(w.dV) * U.reshape((5,) + (1,) * w.dim) * phi0[None]).astype(np.complex128)
+
+
 def batched_spin1_2d(count: int = 512) -> list:
     """Batched spin-1 2D sweep: instance i has n = (64,128,256)[i mod 3] per axis
     on [-10,10]^2, harmonic, beta0 = 100, beta1_i ~ U[-2,2], M_i ~ U[0,0.9]

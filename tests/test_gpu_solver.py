@@ -12,6 +12,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import sbec_oracle as O  # noqa: E402
 from paper_1907_01194_gb300 import workloads as W  # noqa: E402
+from tests.conftest import golden  # noqa: E402
 from tests.oracle_helpers import paper_spin2_1d  # noqa: E402
 
 
@@ -83,6 +84,24 @@ def test_paper_spin2_1d_case_I_energy(dev):
         st = h.solve(X, tol=1e-9)
     assert st["converged"]
     assert abs(st["energy"] - 10.3700300090) < 1e-9
+
+
+@pytest.mark.parametrize("M,E_printed,_t", [tuple(map(float, r)) for r in golden("spin2_2d_energies.txt")])
+def test_paper_spin2_2d_energies(M, E_printed, _t, dev):
+    # Sec. 7.1 spin-2 2D table (tests/golden/spin2_2d_energies.txt): cascadic
+    # 64^2 -> 128^2 -> 256^2 (the coarse levels are the reading n/4, n/2), tol 1e-6
+    from paper_1907_01194_gb300 import sbec
+    ws = [W.paper_spin2_2d(M, n) for n in (64, 128, 256)]
+    hs = [sbec.Handle.from_workload(w) for w in ws]
+    states = [torch.from_numpy(W.paper_nematic_initial(ws[0])).to(dev)] + [
+        torch.empty((5, n, n), dtype=torch.complex128, device=dev) for n in (128, 256)]
+    try:
+        st = sbec.solve_cascadic(hs, states, tol=1e-6, tol_coarse=1e-5)
+    finally:
+        for h in hs:
+            h.close()
+    assert st["converged"] and st["grad_norm"] <= 1e-6
+    assert abs(st["energy"] - E_printed) <= 5e-5
 
 
 def test_host_array_solve_matches_device(dev):
