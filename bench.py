@@ -597,21 +597,25 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
 # The paper's spin-2 2D case (Sec. 7.1, table of spin-2 results in 2D, ARNT with R1):
 # printed energy f and time in seconds (MATLAB R2018b on 12 Xeon E5-2680 v3 cores)
 PAPER_SPIN2_2D = {0.0: (14.3386, 8.3), 0.5: (14.3730, 13.5), 1.5: (14.6754, 13.5)}
+# and its spin-1 2D case (table of spin-1 results in 2D, ARNT with R1)
+PAPER_SPIN1_2D = {0.0: (15.1032, 17.0), 0.2: (15.1411, 19.9), 0.5: (15.3436, 27.2), 0.9: (15.9621, 23.8)}
 
 
 def paper_case(args, sbec, torch, dev, stream):
-    """Context: the paper's spin-2 2D solves (cascadic 64^2 -> 128^2 -> 256^2, R1, the
-    paper's tolerances 1e-5 / 1e-6 and nematic initial data) timed on this GPU next to
+    """Context: the paper's spin-2 and spin-1 2D solves (cascadic from n/4 and n/2, R1,
+    the paper's tolerances 1e-5 / 1e-6 and initial spinors) timed on this GPU next to
     the paper's printed energies and CPU times."""
     runs = []
-    for M, (e_printed, t_paper) in PAPER_SPIN2_2D.items():
-        ws = [W.paper_spin2_2d(M, n) for n in (64, 128, 256)]
+    cases = [("spin-2 2D 256^2", W.paper_spin2_2d, (64, 128, 256), M, e, t) for M, (e, t) in PAPER_SPIN2_2D.items()]
+    cases += [("spin-1 2D 512^2", W.paper_spin1_2d, (128, 256, 512), M, e, t) for M, (e, t) in PAPER_SPIN1_2D.items()]
+    for name, make, levels, M, e_printed, t_paper in cases:
+        ws = [make(M, n) for n in levels]
         hs = [sbec.Handle.from_workload(w, stream=stream.cuda_stream) for w in ws]
         for h, w in zip(hs, ws):
             if not args.no_autotune:
-                h.autotune(torch.from_numpy(W.paper_nematic_initial(w)).to(dev))
-        states = [torch.from_numpy(W.paper_nematic_initial(ws[0])).to(dev)] + [
-            torch.empty((5, n, n), dtype=torch.complex128, device=dev) for n in (128, 256)]
+                h.autotune(torch.from_numpy(W.paper_initial(w)).to(dev))
+        states = [torch.from_numpy(W.paper_initial(ws[0])).to(dev)] + [
+            torch.empty((ws[0].C,) + w.shape, dtype=torch.complex128, device=dev) for w in ws[1:]]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = sbec.solve_cascadic(hs, states, tol=1e-6, tol_coarse=1e-5)
@@ -619,10 +623,11 @@ def paper_case(args, sbec, torch, dev, stream):
         dt = time.perf_counter() - t0
         for h in hs:
             h.close()
-        runs.append({"M": M, "seconds": dt, "energy": st["energy"], "grad_norm": st["grad_norm"],
+        runs.append({"case": name, "M": M, "seconds": dt, "energy": st["energy"], "grad_norm": st["grad_norm"],
                      "paper_energy": e_printed, "paper_seconds": t_paper,
                      "speedup_vs_paper": t_paper / dt if dt > 0 else None})
-    return {"case": "spin-2 2D, 256^2 x 5, beta = (243, 12.1, -13), [-8,8]^2 (paper Sec. 7.1)",
+    return {"cases": "paper Sec. 7.1: spin-2 2D 256^2 x 5, beta = (243, 12.1, -13), [-8,8]^2; "
+                     "spin-1 2D 512^2 x 3, beta = (300, 100), [-16,16]^2",
             "paper_hardware": "MATLAB R2018b, 12 x Intel Xeon E5-2680 v3 (context, not the target)",
             "runs": runs}
 

@@ -168,11 +168,38 @@ def paper_spin2_2d(M: float, n: int = 256) -> Workload:
                     beta=(243.0, 12.1, -13.0, 0.0), M=M, lattice_amp=10.0, lattice_k=np.pi / 2)
 
 
-def paper_nematic_initial(w: Workload) -> np.ndarray:
-    """The paper's initial data for nematic spin-2 interactions (Sec. 7):
-    U phi_0 with U = (sqrt(2+M)/2, 0, 0, 0, sqrt(2-M)/2) and
-    phi_0 = pi^{-d/4} exp(-|x|^2/2), scaled by sqrt(dV); complex128, (5,) + w.shape."""
-    assert w.F == 2
+def paper_spin1_2d(M: float, n: int = 512) -> Workload:
+    """The paper's antiferromagnetic spin-1 2D case (Sec. 7.1): beta = (300, 100),
+    box [-16,16]^2, n = 2^9 per axis, V = |x|^2/2 + 10 sum sin^2(pi x_i / 2).  The text
+    prints sin^2(pi x_i / 4); the energies of its table belong to pi x_i / 2 (with it the
+    printed values are reproduced to all four decimals, with pi x_i / 4 they are not)."""
+    return Workload(f"paper_spin1_2d_n{n}", F=1, n=(n, n), lo=(-16.0, -16.0), hi=(16.0, 16.0),
+                    beta=(300.0, 100.0, 0.0, 0.0), M=M, lattice_amp=10.0, lattice_k=np.pi / 2)
+
+
+def paper_spin1_3d(M: float, n: int = 256) -> Workload:
+    """The paper's ferromagnetic spin-1 3D case (Sec. 7.1): V = sum (x_i^2 +
+    200 sin^2(pi x_i / 2)) / 2, beta = (880, -4.1), box [-16,16]^3, n = 2^8 per axis."""
+    return Workload(f"paper_spin1_3d_n{n}", F=1, n=(n, n, n), lo=(-16.0,) * 3, hi=(16.0,) * 3,
+                    beta=(880.0, -4.1, 0.0, 0.0), M=M, lattice_amp=100.0, lattice_k=np.pi / 2)
+
+
+def paper_spinor(w: Workload) -> np.ndarray:
+    """The paper's initial spinor U (Sec. 7) for the interaction type of w: spin-1
+    ferromagnetic (beta1 <= 0) or antiferromagnetic, spin-2 nematic."""
+    M = w.M
+    if w.F == 1 and w.beta[1] <= 0.0:
+        return np.array([np.sqrt(1.0 + 3.0 * M) / 2.0, np.sqrt((1.0 - M) / 2.0), np.sqrt(1.0 - M) / 2.0])
+    if w.F == 1:
+        return np.array([np.sqrt((1.0 + M) / 2.0), 0.0, np.sqrt((1.0 - M) / 2.0)])
+    if w.F == 2 and w.beta[2] < 0.0 and w.beta[2] < 20.0 * w.beta[1]:
+        return np.array([np.sqrt(2.0 + M) / 2.0, 0.0, 0.0, 0.0, np.sqrt(2.0 - M) / 2.0])
+    raise ValueError("no initial spinor of the paper for this case")
+
+
+def paper_initial(w: Workload) -> np.ndarray:
+    """The paper's initial data U phi_0 (Sec. 7) with phi_0 = pi^{-d/4} exp(-|x|^2/2),
+    scaled by sqrt(dV); complex128, (C,) + w.shape."""
     axes = grid_axes(w)
     r2 = np.zeros(w.shape)
     for i, x in enumerate(axes):
@@ -180,8 +207,14 @@ def paper_nematic_initial(w: Workload) -> np.ndarray:
         sh[w.dim - 1 - i] = w.n[i]
         r2 = r2 + (x ** 2).reshape(sh)
     phi0 = np.pi ** (-w.dim / 4.0) * np.exp(-r2 / 2.0)
-    U = np.array([np.sqrt(2.0 + w.M) / 2.0, 0.0, 0.0, 0.0, np.sqrt(2.0 - w.M) / 2.0])
-    return (np.sqrt(w.dV) * U.reshape((5,) + (1,) * w.dim) * phi0[None]).astype(np.complex128)
+    U = paper_spinor(w)
+    return (np.sqrt(w.dV) * U.reshape((w.C,) + (1,) * w.dim) * phi0[None]).astype(np.complex128)
+
+
+def paper_nematic_initial(w: Workload) -> np.ndarray:
+    """paper_initial for the nematic spin-2 case."""
+    assert w.F == 2
+    return paper_initial(w)
 
 
 def batched_spin1_2d(count: int = 512) -> list:

@@ -104,6 +104,24 @@ def test_paper_spin2_2d_energies(M, E_printed, _t, dev):
     assert abs(st["energy"] - E_printed) <= 5e-5
 
 
+@pytest.mark.parametrize("M,E_printed,_t", [tuple(map(float, r)) for r in golden("spin1_2d_energies.txt")])
+def test_paper_spin1_2d_energies(M, E_printed, _t, dev):
+    # Sec. 7.1 spin-1 2D table (tests/golden/spin1_2d_energies.txt): cascadic
+    # 128^2 -> 256^2 -> 512^2, tol 1e-6
+    from paper_1907_01194_gb300 import sbec
+    ws = [W.paper_spin1_2d(M, n) for n in (128, 256, 512)]
+    hs = [sbec.Handle.from_workload(w) for w in ws]
+    states = [torch.from_numpy(W.paper_initial(ws[0])).to(dev)] + [
+        torch.empty((3, n, n), dtype=torch.complex128, device=dev) for n in (256, 512)]
+    try:
+        st = sbec.solve_cascadic(hs, states, tol=1e-6, tol_coarse=1e-5)
+    finally:
+        for h in hs:
+            h.close()
+    assert st["converged"] and st["grad_norm"] <= 1e-6
+    assert abs(st["energy"] - E_printed) <= 5e-5
+
+
 def test_host_array_solve_matches_device(dev):
     from paper_1907_01194_gb300 import sbec
     w = CASES[0][0]
