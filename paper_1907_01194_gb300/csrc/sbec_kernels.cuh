@@ -1303,16 +1303,6 @@ static int elem_blocks(long long G, int num_sms, int B = 1, int per_sm = 0) {
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
-// In 2D and 3D the inverse x pass only transforms and a grid-stride kernel applies
-// the nonlinear epilogue: fused, the epilogue's registers cap the pass at one block
-// per SM (in FP32 it is bound by memory, in FP64 the rows split unevenly over the
-// SMs); measured, the split form is as fast on 256^2 and 10% faster on 128^3 in
-// FP64, and 4x faster on 256^3 in FP32.  1D problems keep the fused single kernel.
-template <typename T>
-static bool split_epilogue(const Geom& g) {
-    return g.dim > 1;
-}
-
 static PointParams point_params(const Geom& g) {
     PointParams pp;
     for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
@@ -1529,27 +1519,23 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         if (st) return st;
         st = middle_passes<T>(g, w, s);
         if (st) return st;
-        if (split_epilogue<T>(g)) {
-            // inverse x-FFT in place, then the pointwise epilogue at full occupancy
-            st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
-            if (st) return st;
-            const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-            XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
-            a.X = X;
-            st = launch_epi<T, F, false>(g, w, a, ne, s);
-            if (st) return st;
-            SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                        SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
-            goto rgrad;
-        }
-        XArgs a = xargs<T>(g, c, w.work, gout, w.partA);
-        a.X = X;
-        st = launch_x<T, F, X_INV_GRAD>(c, a, w, s);
+        // In 2D and 3D the inverse x pass only transforms and a separate kernel applies
+        // the nonlinear epilogue: fused, the epilogue's registers cap the pass at one
+        // block per SM; measured, the split form is as fast on 256^2 and faster on 128^3
+        // in FP64, and 4x faster on 256^3 in FP32.  1D problems keep the fused kernel.
+        st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
         if (st) return st;
+        const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
+        XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
+        a.X = X;
+        st = launch_epi<T, F, false>(g, w, a, ne, s);
+        if (st) return st;
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                    SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
     }
-    SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
-rgrad:
+    if (g.dim == 1)
+        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
+                    SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
     if (Griem || want_norm) {
         const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
         SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
@@ -1619,22 +1605,19 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (st) return st;
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
-        if (split_epilogue<T>(g)) {
-            st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
-            if (st) return st;
-            const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-            st = launch_epi<T, F, true>(g, w, a, ne, s);
-            if (st) return st;
-            if (riem) {
-                SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
-                            S_PA, S_PB, 0, g.imap);
-                SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
-                            w.partB, g.imap);
-            }
-            return SBEC_OK;
-        }
-        st = launch_x<T, F, X_INV_HESS>(c, a, w, s);
+        // inverse x-FFT in place, then the Hessian epilogue (split as in grad_F)
+        st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
         if (st) return st;
+        const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
+        st = launch_epi<T, F, true>(g, w, a, ne, s);
+        if (st) return st;
+        if (riem) {
+            SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
+                        S_PA, S_PB, 0, g.imap);
+            SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
+                        w.partB, g.imap);
+        }
+        return SBEC_OK;
     }
     if (riem) {
         SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA,
