@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
 // (e1, e2) of pencil w: sm[e2 * rs + e1 * W + w], rs = N1 W + pad; pad = W for
 // W < 16 puts the level-B reads of a half-warp on distinct banks.
 template <typename T, int MODE, int LOGN>
-__global__ void __launch_bounds__(256, 2) k_spass2(const SArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_spass2(const SArgs a) {
     using T2 = typename C2<T>::t;
     constexpr int N1 = Split2<LOGN>::N1, N2 = Split2<LOGN>::N2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -530,10 +530,10 @@ __global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
 // blockIdx.y is the instance; partials of instance b are blocks b*gridDim.x ...
 //
 // The inputs of a point (X, L X, Z: C values each, and V) reach shared memory by
-// per-thread asynchronous copies (cp.async) one grid-stride step ahead: while a
-// thread computes point k, the copies of point k + 1 are in flight, so the
-// register-heavy pointwise algebra (one or two blocks per SM) overlaps the HBM
-// traffic.  Each thread reads back only the slots it copied itself.
+// per-thread asynchronous copies (cp.async) one or two grid-stride steps ahead:
+// while a thread computes point k, the copies of the next points are in flight,
+// so the register-heavy pointwise algebra (one or two blocks per SM) overlaps the
+// HBM traffic.  Each thread reads back only the slots it copied itself.
 // ---------------------------------------------------------------------------
 constexpr int kEpiThreads = 256;
 
@@ -550,9 +550,19 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T, int F, bool HESS>
-constexpr size_t epi_smem() {
-    return 2 * ((size_t)(HESS ? 3 : 2) * (2 * F + 1) * kEpiThreads * sizeof(typename C2<T>::t) +
-                (size_t)kEpiThreads * sizeof(T));
+__host__ __device__ constexpr size_t epi_stage_bytes() {
+    return (size_t)(HESS ? 3 : 2) * (2 * F + 1) * kEpiThreads * sizeof(typename C2<T>::t) +
+           (size_t)kEpiThreads * sizeof(T);
+}
+// copies in flight: points k + 1 and k + 2 while point k is computed, when three
+// stages fit in 200 KB of shared memory, else point k + 1 only
+template <typename T, int F, bool HESS>
+__host__ __device__ constexpr int epi_stages() {
+    return 3 * epi_stage_bytes<T, F, HESS>() <= 200 * 1024 ? 3 : 2;
+}
+template <typename T, int F, bool HESS>
+__host__ __device__ constexpr size_t epi_smem() {
+    return epi_stages<T, F, HESS>() * epi_stage_bytes<T, F, HESS>();
 }
 
 template <typename T, int F, bool HESS>
@@ -562,6 +572,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
     constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
     constexpr int NA = HESS ? 3 : 2;                  // staged arrays X, L X (, Z)
     constexpr int P = kEpiThreads;
+    constexpr int NS = epi_stages<T, F, HESS>();
     const long long inst = inst_of(a.imap, blockIdx.y);
     const long long foff = inst * (long long)C * G;
     const T2* __restrict__ LX = reinterpret_cast<const T2*>(lxp) + foff;
@@ -573,8 +584,8 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
     if (skipped(a.skip, inst)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* stg = reinterpret_cast<T2*>(smem_raw);                       // [2][NA C][P]
-    T* vst = reinterpret_cast<T*>(stg + 2 * NA * C * P);             // [2][P]
+    T2* stg = reinterpret_cast<T2*>(smem_raw);                       // [NS][NA C][P]
+    T* vst = reinterpret_cast<T*>(stg + NS * NA * C * P);            // [NS][P]
     const int tid = threadIdx.x;
     T shift[C];
     if (HESS) hess_shift<F, T>(a, scal, shift);
@@ -595,15 +606,17 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
         cp_async_commit();
     };
     long long pt = (long long)blockIdx.x * P + tid;
-    issue(pt, 0);
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) issue(pt + k * stride, k);
     for (int k = 0; pt < G; ++k, pt += stride) {
-        issue(pt + stride, (k + 1) & 1);
-        cp_async_wait<1>();                          // this thread's copies of point pt are in
-        const T2* sx = stg + (size_t)(k & 1) * NA * C * P + tid;
+        issue(pt + (NS - 1) * stride, (k + NS - 1) % NS);
+        cp_async_wait<NS - 1>();                     // this thread's copies of point pt are in
+        const int sk = k % NS;
+        const T2* sx = stg + (size_t)sk * NA * C * P + tid;
         T2 x[C], l[C], o[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) { x[c] = sx[c * P]; l[c] = sx[(C + c) * P]; }
-        const T V = vst[(k & 1) * P + tid];
+        const T V = vst[sk * P + tid];
         Dens<F, T2> D;
         D.compute(x);
         if (!HESS) {
