@@ -70,10 +70,10 @@ PW_FLOPS = {"grad": {1: 170, 2: 375, 3: 760}, "hess": {1: 300, 2: 640, 3: 1400},
 # (kernel, workload); profiles/ holds the summaries
 NCU_TRAFFIC = {
     # full capture of the 256^2 FP64 workload (the state stays in L2: one read per field)
-    ("s_k2", "spin2_2d_256x256"): 5328640.0,
+    ("s_k2", "spin2_2d_256x256"): 5328128.0,
     # 128^3 capture of the same kernel scaled by the 8x larger fields (writes partly held in
     # L2 at 128^3, so this is a lower bound at 256^3)
-    ("proj_apply", "spin3_3d_256cubed"): 8 * (234901760.0 + 73311232.0),
+    ("proj_apply", "spin3_3d_256cubed"): 8 * (234903040.0 + 73547264.0),
 }
 
 
