@@ -16,7 +16,9 @@
  *
  * Pointers: every array argument may be a device pointer or a host pointer
  * (pageable or pinned); host arrays are staged through the handle's
- * workspace with copies on the handle's stream.  The caller owns all state
+ * workspace with copies on the handle's stream, except page-locked input
+ * arrays of at most 1 MiB, which the kernels read in place over the CPU-GPU
+ * link.  The caller owns all state
  * arrays; the library owns its workspace (allocated by sbec_create, freed by
  * sbec_destroy).  No other call allocates memory.
  *

@@ -139,6 +139,33 @@ def test_host_pointers_match_device(dev):
     assert np.array_equal(Gd.cpu().numpy(), Gh)
 
 
+def test_pinned_host_arrays_match_device(dev):
+    # page-locked host arrays are read in place by the kernels; results equal the
+    # device-array results bit for bit
+    sbec = _sbec()
+    w = CASES[5]
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    Z = torch.from_numpy(Zf).to(dev)
+    Xp = torch.from_numpy(Xf).pin_memory()
+    Zp = torch.from_numpy(Zf).pin_memory()
+    Gd, Hd, Rd = (torch.empty_like(X) for _ in range(3))
+    Gp, Hp, Rp = (torch.empty_like(Xp).pin_memory() for _ in range(3))
+    with sbec.Handle.from_workload(w) as h:
+        a = h.grad(X, G_riem=Gd)
+        h.hessvec(X, Z, Hd, sigma=0.4, riemannian=True)
+        h.retract(X, Gd, -1e-3, 1, Rd)
+        Ed = h.energy(Rd)
+        h.sync()
+        b = h.grad(Xp, G_riem=Gp)
+        h.hessvec(Xp, Zp, Hp, sigma=0.4, riemannian=True)
+        h.retract(Xp, Gp, -1e-3, 1, Rp)
+        Ep = h.energy(Rp)
+    assert a == b and Ed == Ep
+    for dv, hv in ((Gd, Gp), (Hd, Hp), (Rd, Rp)):
+        assert torch.equal(dv.cpu(), hv)
+
+
 def test_host_riemannian_hessvec_uses_the_gradient_at_the_same_pointer(dev):
     # the Lemma 4.2 coefficients come from the latest sbec_grad at the same X pointer,
     # host or device; a new pointer recomputes them
