@@ -519,9 +519,11 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
     if args.workload == "batch512":
         out = {"tol": tol, "classes": []}
         t_all = 0.0
+        t_mix = 0.0
         for h, _, ws in groups:
-            X = torch.from_numpy(np.stack([W.initial_fields(x) for x in ws])).to(dev).to(
+            X0 = torch.from_numpy(np.stack([W.initial_fields(x) for x in ws])).to(dev).to(
                 torch.complex128 if args.precision == "fp64" else torch.complex64)
+            X = X0.clone()
             nb = 10 * X.numel() * X.element_size()
             ws_buf = torch.empty(nb, dtype=torch.uint8, device=dev)
             torch.cuda.synchronize()
@@ -530,12 +532,34 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             t_all += dt
-            out["classes"].append({"grid": list(ws[0].n), "instances": len(ws), "seconds": dt,
-                                   "converged": int(sum(s["converged"] for s in sts)),
-                                   "max_outer": int(max(s["outer_iters"] for s in sts)),
-                                   "max_inner": int(max(s["inner_iters"] for s in sts)),
-                                   "energies_head": [s["energy"] for s in sts[:3]]})
+            cls = {"grid": list(ws[0].n), "instances": len(ws), "seconds": dt,
+                   "converged": int(sum(s["converged"] for s in sts)),
+                   "max_outer": int(max(s["outer_iters"] for s in sts)),
+                   "max_inner": int(max(s["inner_iters"] for s in sts)),
+                   "energies_head": [s["energy"] for s in sts[:3]]}
+            del ws_buf
+            if args.precision == "fp64":
+                # mixed form of the same class: FP32 lock-step solve, FP64 refinement
+                h32 = sbec.Handle.batch(ws, precision="mixed", stream=stream.cuda_stream)
+                if not args.no_autotune:
+                    h32.autotune(X0.to(torch.complex64))
+                Xm = X0.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sm, sf = sbec.solve_mixed(h, h32, Xm, tol=tol, tol_mixed=1e-3)
+                torch.cuda.synchronize()
+                dm = time.perf_counter() - t0
+                t_mix += dm
+                h32.close()
+                cls["mixed_refined"] = {
+                    "seconds": dm, "converged": int(sum(s["converged"] for s in sf)),
+                    "max_energy_rel_diff": max(abs(a["energy"] - b["energy"]) / abs(b["energy"])
+                                               for a, b in zip(sf, sts))}
+            out["classes"].append(cls)
         out["fp64" if args.precision == "fp64" else "mixed"] = {"seconds": t_all}
+        if args.precision == "fp64":
+            out["mixed_refined"] = {"seconds": t_mix}
+            out["speedup_mixed_over_fp64"] = t_all / t_mix if t_mix > 0 else None
         return out
     h = groups[0][0]
     X0 = torch.from_numpy(W.initial_fields(w)).to(dev)

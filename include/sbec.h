@@ -178,9 +178,12 @@ int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void*
 
 /* Mixed-precision solve with FP64 refinement: X (complex128, device) is cast to
  * float, solved on h32 (precision SBEC_MIXED, same problem and stream as h64)
- * to max(tol_mixed, opts->tol), cast back, projected on M and refined on h64
- * (SBEC_FP64) to opts->tol.  Stats of both phases are returned.  workspace:
- * device memory of at least sbec_solve_mixed_workspace_bytes. */
+ * to max(tol_mixed, opts->tol) or at most 300 iterations, cast back, projected
+ * on M and refined on h64 (SBEC_FP64) to opts->tol.  Stats of both phases are
+ * returned.  Batch handles
+ * (the same instances in both) run both phases with sbec_solve_batch; the stats
+ * arrays then have B entries.  workspace: device memory of at least
+ * sbec_solve_mixed_workspace_bytes. */
 int sbec_solve_mixed_workspace_bytes(const sbec_handle* h64, const sbec_handle* h32, size_t* bytes);
 int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_solve_opts* opts, double tol_mixed,
                      void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64);

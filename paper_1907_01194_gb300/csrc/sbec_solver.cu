@@ -944,6 +944,7 @@ int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_sol
     if (!h64 || !h32 || !X || !workspace) return SBEC_ERR_ARG;
     if (h64->prob.precision != SBEC_FP64 || h32->prob.precision != SBEC_MIXED) return SBEC_ERR_ARG;
     if (h64->geom.G != h32->geom.G || h64->geom.C != h32->geom.C || h64->stream != h32->stream) return SBEC_ERR_ARG;
+    if (h64->B != h32->B) return SBEC_ERR_ARG;
     size_t need = 0;
     sbec_solve_mixed_workspace_bytes(h64, h32, &need);
     if (workspace_bytes < need || !sbec_is_device_ptr(X) || !sbec_is_device_ptr(workspace)) return SBEC_ERR_ARG;
@@ -953,19 +954,28 @@ int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_sol
     void* ws64 = base;
     void* X32 = base + 10 * h64->field_bytes;
     void* ws32 = base + 10 * h64->field_bytes + h32->field_bytes;
-    const long long nreal = 2LL * h64->geom.C * h64->geom.G;
+    const long long nreal = 2LL * h64->B * h64->geom.C * h64->geom.G;
+    // one solve per phase: the lock-step batch solver for batch handles
+    auto phase = [&](sbec_handle* h, void* Xp, const sbec_solve_opts* po, void* ws, sbec_stats* st) {
+        return h->B > 1 ? sbec_solve_batch(h, Xp, po, ws, 10 * h->field_bytes, st)
+                        : sbec_solve(h, Xp, po, ws, 10 * h->field_bytes, st);
+    };
     const int blocks = 4 * h64->work.num_sms;
     k_cast<double, float><<<blocks, 256, 0, h64->stream>>>(static_cast<const double*>(X), static_cast<float*>(X32), nreal);
     if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
     sbec_solve_opts om = o;
     om.tol = tol_mixed > o.tol ? tol_mixed : o.tol;
-    int rc = sbec_solve(h32, X32, &om, ws32, 10 * h32->field_bytes, st_mixed);
+    // the FP32 phase only has to get close: below its rounding floor ARNT can stall
+    // short of tol_mixed, so it stops after at most 300 iterations and the FP64
+    // phase completes the solve from wherever it got
+    if (om.maxit > 300) om.maxit = 300;
+    int rc = phase(h32, X32, &om, ws32, st_mixed);
     if (rc != SBEC_OK && rc != SBEC_ERR_NOCONV) return rc;
     k_cast<float, double><<<blocks, 256, 0, h64->stream>>>(static_cast<const float*>(X32), static_cast<double*>(X), nreal);
     if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
     sbec_solve_opts of = o;
     of.project_initial = 1;            // the float state is back on M to double precision
-    return sbec_solve(h64, X, &of, ws64, 10 * h64->field_bytes, st_fp64);
+    return phase(h64, X, &of, ws64, st_fp64);
 }
 
 // Cascadic multigrid (Algorithm 1, outer loop over meshes).

@@ -405,7 +405,8 @@ _lib.sbec_solve_mixed.restype = _int
 def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction=1, maxit=10000,
                 rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None, graphs=None):
     """Mixed-precision solve on h32 then FP64 refinement on h64 (sbec_solve_mixed).
-    X: complex128 device tensor, overwritten.  Returns (stats_mixed, stats_fp64)."""
+    X: complex128 device tensor, overwritten.  Returns (stats_mixed, stats_fp64), dicts
+    for single handles and lists of B dicts for batch handles."""
     o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_mixed_workspace_bytes(h64._h, h32._h, ctypes.byref(nb)),
@@ -413,15 +414,15 @@ def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction
     if workspace is None:
         import torch
         workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
-    sm, sf = Stats(), Stats()
+    B = h64.B
+    sm, sf = (Stats * B)(), (Stats * B)()
     rc = _lib.sbec_solve_mixed(h64._h, h32._h, _ptr(X), ctypes.byref(o), float(tol_mixed), _ptr(workspace),
-                               nb.value, ctypes.byref(sm), ctypes.byref(sf))
+                               nb.value, sm, sf)
     if rc not in (OK, ERR_NOCONV):
         _check(rc, "sbec_solve_mixed")
-    a = {k: getattr(sm, k) for k, _ in Stats._fields_}
-    b = {k: getattr(sf, k) for k, _ in Stats._fields_}
-    b["status"] = rc
-    return a, b
+    a = [{k: getattr(sm[i], k) for k, _ in Stats._fields_} for i in range(B)]
+    b = [dict({k: getattr(sf[i], k) for k, _ in Stats._fields_}, status=rc) for i in range(B)]
+    return (a[0], b[0]) if B == 1 else (a, b)
 
 
 _lib.sbec_prolongate.argtypes = [_vp, _vp, _vp, _vp]

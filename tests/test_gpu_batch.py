@@ -98,3 +98,20 @@ def test_batch_solve_matches_oracle_per_instance(F, n, L, count, dev):
         assert abs(sts[i]["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
         m = np.sum(np.abs(X[i].cpu().numpy().reshape(w.C, -1)) ** 2, axis=1)
         assert abs(m.sum() - 1) < 1e-12 and abs(m @ np.arange(w.F, -w.F - 1, -1) - w.M) < 1e-12
+
+
+def test_batch_mixed_solve_with_fp64_refinement(dev):
+    # a13 x a14: FP32 lock-step batch solve, then FP64 refinement of every instance;
+    # refined energies meet the FP64 oracle's to 1e-10 relative
+    from paper_1907_01194_gb300 import sbec
+    ws = _batch(1, (32, 32), 7.0, 4, seed=8)
+    X0 = np.stack([W.initial_fields(w) for w in ws])
+    X = torch.from_numpy(X0).to(dev)
+    with sbec.Handle.batch(ws) as h64, sbec.Handle.batch(ws, precision="mixed") as h32:
+        sm, sf = sbec.solve_mixed(h64, h32, X, tol=1e-9, tol_mixed=1e-3)
+    assert len(sm) == len(sf) == len(ws)
+    for i, w in enumerate(ws):
+        P = O.Problem(F=w.F, n=w.n, lo=w.lo, hi=w.hi, beta=w.beta, V=W.potential(w), M=w.M)
+        Xs, ost, _ = O.solve(P, O.to_matrix(P, X0[i]), O.SolveOptions(tol=1e-9))
+        assert sf[i]["converged"] and ost.converged
+        assert abs(sf[i]["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
