@@ -18,6 +18,7 @@ enum {
     S_NORM2 = 10,      // scratch squared norm
     S_XFORM = 11,      // reserved
     S_SKIP = 12,       // nonzero: every kernel leaves this instance of a batch untouched
+    S_TICKET = 13,     // blocks of the running launch that have stored their partials
     S_SIG = 16,        // 7 retraction scales sigma_l (component index order)
     S_SOLVER = 32,     // solver scalars start here
     S_COUNT = 128

@@ -15,6 +15,8 @@
 
 #include <math.h>
 
+#include <atomic>
+
 #include "sbec_device.cuh"
 #include "sbec_internal.h"
 
@@ -30,6 +32,186 @@ __device__ __forceinline__ bool skipped(const double* scal0, long long inst) {
 // Partial sums are laid out by slot, data and scalar blocks by instance.
 __device__ __forceinline__ long long inst_of(const int* imap, long long slot) {
     return imap ? (long long)imap[slot] : slot;
+}
+
+// ---------------------------------------------------------------------------
+// Finalize steps: fixed-order sums of the partials and the scalar algebra of
+// Lemma 4.1 / 4.2 and of the retractions, run by one block per instance (the
+// last block of the kernel that stored the partials, or a one-block kernel).
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void set_status(double* scal, int code) {
+    if (scal[SBEC_S_STATUS] == 0.0) scal[SBEC_S_STATUS] = double(code);
+}
+
+// Block-parallel fixed-order sums of nq partial quantities.  With nw warps, each
+// quantity gets wq = max(1, nw / nq) warps; warp j of quantity k sums the
+// lane-strided elements part*32 + lane + i * wq * 32 (part = j) and a shuffle
+// tree, then thread k adds the wq warp sums in order, so every sum has an order
+// fixed by the block size.  Quantity q of instance b is partials[q * ntot + off ..
+// off + cnt - 1] with off = b * cnt.  vals[k] is valid after the barrier.  Every
+// block that calls it has a multiple of 32 threads (all launch shapes do).
+// U loads of a lane are in flight at a time (the order of the sums is the same for
+// every U).  U = 1 in the tail of k_dot_reduce: with U = 8 there, the FP32 spin-3
+// kernel took 0.57 instead of 0.38 ms on 256^3 fields (its main loop, unchanged in
+// the source, was compiled differently).
+template <int U = 8>
+__device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int ntot, int off, int cnt, const int* qs,
+                                          int nq, double* vals) {
+    __shared__ double part_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int wq = nq < nw ? nw / nq : 1;
+    for (int j = warp; j < nq * wq; j += nw) {
+        const int k = j / wq, part = j - k * wq;
+        const double* src = pa + (size_t)qs[k] * ntot + off;
+        // sequential sum of the lane's elements, U loads in flight at a time
+        const int st = wq * 32;
+        int i = part * 32 + lane;
+        double s = 0.0;
+        if constexpr (U > 1) {
+            for (; i + (U - 1) * st < cnt; i += U * st) {
+                double t[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) t[u] = __ldcg(src + i + u * st);
+#pragma unroll
+                for (int u = 0; u < U; ++u) s += t[u];
+            }
+        }
+        for (; i < cnt; i += st) s += __ldcg(src + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (wq == 1) vals[k] = s;
+            else part_sums[j] = s;
+        }
+    }
+    __syncthreads();
+    if (wq > 1) {
+        if ((int)threadIdx.x < nq) {
+            double s = 0.0;
+            for (int p = 0; p < wq; ++p) s += part_sums[threadIdx.x * wq + p];
+            vals[threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Finalize bodies: instance `inst` sits in launch slot b; its partials are the
+// slice b * na_inst .. of na_inst blocks inside the na_tot blocks of the launch.
+
+// Finalize fused into a producer: every block of instance `inst` stores its
+// partials, then draws a ticket in the instance's scalar block; the block that
+// draws the last one (nblk_slot - 1) runs the finalize on all of them.  Thread 0
+// wrote the block's partials (block_reduce_store) and fences them before its
+// ticket; the last block resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(double* scal, int nblk_slot) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const double t = atomicAdd(scal + S_TICKET, 1.0);
+        last = (t == double(nblk_slot - 1));
+        if (last) scal[S_TICKET] = 0.0;
+        __threadfence();
+    }
+    __syncthreads();
+    return last != 0;
+}
+
+// energy: scal[E] = sum of partA quantities 0..nqa-1 (+ partB quantity 0)
+__device__ __forceinline__ void fin_energy_body(const double* pa, int na_tot, int na_inst, int nqa, const double* pb,
+                                                int nb_tot, int nb_inst, double* scal0, int b, long long inst) {
+    __shared__ double va[4], vb[1];
+    const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
+    warp_sums(pa, na_tot, b * na_inst, na_inst, qa, nqa, va);
+    if (pb) warp_sums(pb, nb_tot, b * nb_inst, nb_inst, qb, 1, vb);
+    if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)inst * S_COUNT;
+        double e = 0.0;
+        for (int q = 0; q < nqa; ++q) e += va[q];
+        if (pb) e += vb[0];
+        scal[SBEC_S_ENERGY] = e;
+        if (!isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
+    }
+}
+
+// gradient / projection coefficients (Lemma 4.1, Eq. ab) from n_l (q = qn + l) and
+// t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
+// beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
+struct FinProj {
+    int on;                 // run by the producer's last block per instance
+    int qe, qn, qt;         // partial quantities: energy (-1: none), n_l, t_l
+    int slot_a, slot_b, write_grad_info;
+    double M0;
+    const double* Mb;
+    double* scal0;          // scalar blocks (tickets and results)
+};
+
+// Energy finalize fused into the Parseval pass: pa holds the x pass's pointwise
+// energy partials (one quantity), the pass's own partials the kinetic term.
+struct FinEnergy {
+    int on;
+    const double* pa;
+    int na_tot, na_inst;
+    double* scal0;
+};
+
+template <int U = 8>
+__device__ __forceinline__ void fin_proj_body(const double* pa, int na_tot, int na_inst, int F, int qe, int qn, int qt,
+                                              double M0, const double* Mb, double* scal0, int slot_a, int slot_b,
+                                              int write_grad_info, int b, long long inst) {
+    const int C = 2 * F + 1;
+    __shared__ double v[15];
+    int qs[15];
+    int nq = 0;
+    for (int i = 0; i < C; ++i) qs[nq++] = qn + i;
+    for (int i = 0; i < C; ++i) qs[nq++] = qt + i;
+    if (qe >= 0) qs[nq++] = qe;
+    warp_sums<U>(pa, na_tot, b * na_inst, na_inst, qs, nq, v);
+    if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)inst * S_COUNT;
+        const double M = Mb ? Mb[inst] : M0;
+        double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, bb = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
+        for (int i = 0; i < C; ++i) {
+            const double l = double(F - i), nl = v[i], tl = v[C + i];
+            a += nl; bb += l * nl; c += l * l * nl;
+            ug += tl; uGg += l * tl;
+        }
+        const double au = c - M * M;
+        const double al = (c * ug - M * uGg) / au;
+        const double be = (uGg - M * ug) / au;
+        if (!isfinite(c) || !isfinite(ug) || !isfinite(uGg) || !isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
+        if (!(au > 0.0)) set_status(scal, SBEC_ERR_DOMAIN);
+        scal[slot_a] = al;
+        scal[slot_b] = be;
+        if (write_grad_info) {
+            scal[SBEC_S_ENERGY] = e;
+            scal[SBEC_S_MASS] = a;
+            scal[SBEC_S_MAG] = bb;
+            scal[S_C2] = c;
+            if (!isfinite(e) || !isfinite(al) || !isfinite(be)) set_status(scal, SBEC_ERR_NONFINITE);
+        }
+    }
+}
+
+// one block per instance: the finalize of a producer that does not run it itself
+static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int F, const FinProj fp,
+                                  const int* imap) {
+    const int b = blockIdx.x;
+    const long long inst = inst_of(imap, b);
+    if (skipped(fp.scal0, inst)) return;
+    fin_proj_body(pa, na_tot, na_inst, F, fp.qe, fp.qn, fp.qt, fp.M0, fp.Mb, fp.scal0, fp.slot_a, fp.slot_b,
+                  fp.write_grad_info, b, inst);
+}
+
+__device__ __forceinline__ void fin_norm_body(const double* pa, int na_tot, int na_inst, double* scal0, int slot,
+                                              int b, long long inst) {
+    __shared__ double v[1];
+    const int q[1] = {0};
+    warp_sums(pa, na_tot, b * na_inst, na_inst, q, 1, v);
+    if (threadIdx.x == 0) {
+        double* scal = scal0 + (size_t)inst * S_COUNT;
+        scal[slot] = v[0];
+        if (!isfinite(v[0])) set_status(scal, SBEC_ERR_NONFINITE);
+    }
 }
 
 #define SBEC_CUDA_TRY(expr)                                   \
@@ -83,6 +265,9 @@ struct XArgs {
     const PointParams* ppb;     // per-instance point parameters (batches) or null
     const double* skip;         // scalar blocks (S_SKIP flags) or null
     const int* imap;            // launch slot -> instance, or null (identity)
+    FinProj fp;                 // fp.on: Lemma 4.1 finalize by the last block per instance
+    int fe;                     // X_FULL_ENERGY: energy finalize by the last block per
+                                // instance, into the scalar blocks fp.scal0
 };
 
 // Shift of the Hessian epilogue per component: sigma (times the instance's
@@ -239,6 +424,13 @@ __global__ void __launch_bounds__(512) k_xpass(const XArgs a) {
         double v[NQ];
         acc_values(acc, v);
         block_reduce_store<NQ>(v, a.partials, a.nblk, blockIdx.x);
+        // 1D passes: the finalize by the last block of the instance
+        const int nb_inst = (int)(a.rpi / RPB);
+        if (MODE == X_FULL_ENERGY && a.fe && last_block(a.fp.scal0 + inst * S_COUNT, nb_inst))
+            fin_energy_body(a.partials, a.nblk, nb_inst, 2, nullptr, 0, 0, a.fp.scal0, (int)slot, inst);
+        if (MODE != X_FULL_ENERGY && a.fp.on && last_block(a.fp.scal0 + inst * S_COUNT, nb_inst))
+            fin_proj_body(a.partials, a.nblk, nb_inst, F, a.fp.qe, a.fp.qn, a.fp.qt, a.fp.M0, a.fp.Mb, a.fp.scal0,
+                          a.fp.slot_a, a.fp.slot_b, a.fp.write_grad_info, (int)slot, inst);
     }
 }
 
@@ -259,9 +451,11 @@ struct SArgs {
     double invG;
     double* partials;
     int nblk;
+    int nblk_inst;        // blocks per instance
     int C;                // components (instance = pencil component / C)
     const double* skip;   // scalar blocks (S_SKIP flags) or null
     const int* imap;      // launch slot -> instance, or null (identity)
+    FinEnergy fe;         // S_PARSEVAL, fe.on: energy finalize by the last block per instance
 };
 
 template <typename T, int MODE, int ITEMS>
@@ -316,6 +510,10 @@ __global__ void __launch_bounds__(512) k_spass(const SArgs a) {
             double v[1];
             acc_values(acc, v);
             block_reduce_store<1>(v, a.partials, a.nblk, blockIdx.x);
+            const int slot = cs / a.C, nb_inst = a.nblk_inst;
+            if (a.fe.on && last_block(a.fe.scal0 + inst * S_COUNT, nb_inst))
+                fin_energy_body(a.fe.pa, a.fe.na_tot, a.fe.na_inst, 1, a.partials, a.nblk, nb_inst, a.fe.scal0, slot,
+                                inst);
             return;
         }
         __syncthreads();
@@ -415,6 +613,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_spass2(const SA
             double r[1];
             acc_values(acc, r);
             block_reduce_store<1>(r, a.partials, a.nblk, blockIdx.x);
+            const int slot = cs / a.C, nb_inst = a.nblk_inst;
+            if (a.fe.on && last_block(a.fe.scal0 + inst * S_COUNT, nb_inst))
+                fin_energy_body(a.fe.pa, a.fe.na_tot, a.fe.na_inst, 1, a.partials, a.nblk, nb_inst, a.fe.scal0, slot,
+                                inst);
             return;
         }
     }
@@ -537,6 +739,12 @@ __global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kEpiThreads = 256;
 
+// Epilogues whose last block per instance runs the Lemma 4.1 finalize.  The F = 3
+// Hessian epilogue keeps a separate finalize launch: with the finalize in its tail
+// ptxas allocated its registers differently (168 instead of 254 in FP32) and the
+// epilogue ran 5-9% slower on the 128^3 (FP64) and 256^3 (FP32) spin-3 grids.
+template <typename T, int F, bool HESS> struct EpiFusedFin { static constexpr bool v = !(HESS && F == 3); };
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -649,6 +857,11 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
     double v[NQ];
     acc_values(acc, v);
     block_reduce_store<NQ>(v, a.partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    if constexpr (EpiFusedFin<T, F, HESS>::v) {
+        if (a.fp.on && last_block(a.fp.scal0 + inst * S_COUNT, gridDim.x))
+            fin_proj_body(a.partials, gridDim.x * gridDim.y, gridDim.x, F, a.fp.qe, a.fp.qn, a.fp.qt, a.fp.M0,
+                          a.fp.Mb, a.fp.scal0, a.fp.slot_a, a.fp.slot_b, a.fp.write_grad_info, blockIdx.y, inst);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -661,7 +874,7 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const v
 // partials: n_l = |u_l|^2 (q = l index), t_l = <u_l, w_l> (q = C + l)
 template <typename T, int F>
 __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* Wp, long long G, double* partials,
-                                                    const double* skip, const int* imap) {
+                                                    const double* skip, const int* imap, const FinProj fp) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     const long long inst = inst_of(imap, blockIdx.y);
@@ -681,13 +894,17 @@ __global__ void __launch_bounds__(256) k_dot_reduce(const void* Up, const void* 
     double v[2 * C];
     acc_values(acc, v);
     block_reduce_store<2 * C>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    if (fp.on && last_block(fp.scal0 + inst * S_COUNT, gridDim.x))
+        fin_proj_body<1>(partials, gridDim.x * gridDim.y, gridDim.x, F, fp.qe, fp.qn, fp.qt, fp.M0, fp.Mb, fp.scal0,
+                      fp.slot_a, fp.slot_b, fp.write_grad_info, blockIdx.y, inst);
 }
 
-// out_l = W_l - (alpha + beta l) U_l with (alpha, beta) = scal[ia], scal[ib]; partial |out|^2
-template <typename T, int F>
+// out_l = W_l - (alpha + beta l) U_l with (alpha, beta) = scal[ia], scal[ib]; with
+// NORM, |out|^2 into scal[norm_slot] (partials, summed by the last block per instance)
+template <typename T, int F, bool NORM>
 __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* Wp, void* Op, long long G,
-                                                    const double* __restrict__ scal0, int ia, int ib,
-                                                    double* partials, const int* imap) {
+                                                    double* scal0, int ia, int ib, double* partials,
+                                                    const int* imap, int norm_slot) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     const long long inst = inst_of(imap, blockIdx.y);
@@ -707,43 +924,17 @@ __global__ void __launch_bounds__(256) k_proj_apply(const void* Up, const void* 
             const T2 u = U[c * G + p];
             T2 w = Wv[c * G + p];
             caxpy(w, -coef[c], u);
-            acc[0].add(cabs2(w));
+            if (NORM) acc[0].add(cabs2(w));
             if (O) O[c * G + p] = w;
         }
     }
-    double v[1];
-    acc_values(acc, v);
-    block_reduce_store<1>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
-}
-
-// w = U + t Xi into out; partials m_l = |w_l|^2
-template <typename T, int F>
-__global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
-                                                   double* partials, const double* __restrict__ scal0, int tslot,
-                                                   const int* imap) {
-    using T2 = typename C2<T>::t;
-    constexpr int C = 2 * F + 1;
-    const long long inst = inst_of(imap, blockIdx.y);
-    if (skipped(scal0, inst)) return;
-    const long long foff = inst * C * G;
-    if (tslot >= 0) t *= scal0[(size_t)inst * S_COUNT + tslot];
-    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
-    const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
-    T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
-    Acc<T> acc[C];
-    const T tt = T(t);
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            T2 w = U[c * G + p];
-            caxpy(w, tt, Xi[c * G + p]);
-            acc[c].add(cabs2(w));
-            O[c * G + p] = w;
-        }
+    if (NORM) {
+        double v[1];
+        acc_values(acc, v);
+        block_reduce_store<1>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+        if (last_block(scal0 + inst * S_COUNT, gridDim.x))
+            fin_norm_body(partials, gridDim.x * gridDim.y, gridDim.x, scal0, norm_slot, blockIdx.y, inst);
     }
-    double v[C];
-    acc_values(acc, v);
-    block_reduce_store<C>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // out_l *= scal[S_SIG + l]
@@ -766,112 +957,6 @@ __global__ void __launch_bounds__(256) k_scale(void* Op, long long G, const doub
     }
 }
 
-// ---------------------------------------------------------------------------
-// Finalize kernels (one block of 256 threads): fixed-order sums of the
-// partials and the scalar algebra of Lemma 4.1 / 4.2 and of the retractions.
-// ---------------------------------------------------------------------------
-static __device__ __forceinline__ void set_status(double* scal, int code) {
-    if (scal[SBEC_S_STATUS] == 0.0) scal[SBEC_S_STATUS] = double(code);
-}
-
-// Warp-parallel fixed-order sums: warp w of the block reduces quantities
-// q = w, w + nwarps, ...; lane-strided loads then a shuffle tree, so each sum
-// has a fixed order.  Quantity q of instance b is partials[q * ntot + off ..
-// off + cnt - 1] with off = b * cnt.  vals[k] is valid after the barrier.
-__device__ __forceinline__ void warp_sums(const double* __restrict__ pa, int ntot, int off, int cnt, const int* qs,
-                                          int nq, double* vals) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = warp; k < nq; k += nw) {
-        const double* src = pa + (size_t)qs[k] * ntot + off;
-        double s = 0.0;
-        for (int i = lane; i < cnt; i += 32) s += src[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) vals[k] = s;
-    }
-    __syncthreads();
-}
-
-// Finalize kernels: one block per instance (blockIdx.x), whose partials are the
-// per-instance slices of na_inst blocks inside the na_tot blocks of the launch.
-
-// energy: scal[E] = sum of partA quantities 0..nqa-1 (+ partB quantity 0)
-static __global__ void k_fin_energy(const double* pa, int na_tot, int na_inst, int nqa, const double* pb, int nb_tot,
-                                    int nb_inst, double* scal0, const int* imap) {
-    __shared__ double va[4], vb[1];
-    const int b = blockIdx.x;
-    const long long inst = inst_of(imap, b);
-    if (skipped(scal0, inst)) return;
-    const int qa[4] = {0, 1, 2, 3}, qb[1] = {0};
-    warp_sums(pa, na_tot, b * na_inst, na_inst, qa, nqa, va);
-    if (pb) warp_sums(pb, nb_tot, b * nb_inst, nb_inst, qb, 1, vb);
-    if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)inst * S_COUNT;
-        double e = 0.0;
-        for (int q = 0; q < nqa; ++q) e += va[q];
-        if (pb) e += vb[0];
-        scal[SBEC_S_ENERGY] = e;
-        if (!isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
-    }
-}
-
-// gradient / projection coefficients (Lemma 4.1, Eq. ab) from n_l (q = qn + l) and
-// t_l (q = qt + l): alpha_w = (c u^T w - M u^T Gamma w)/(c - M^2),
-// beta_w = (u^T Gamma w - M u^T w)/(c - M^2), c = u^T Gamma^2 u.
-static __global__ void k_fin_proj(const double* pa, int na_tot, int na_inst, int F, int qe, int qn, int qt, double M0,
-                                  const double* Mb, double* scal0, int slot_a, int slot_b, int write_grad_info,
-                                  const int* imap) {
-    const int C = 2 * F + 1;
-    const int b = blockIdx.x;
-    const long long inst = inst_of(imap, b);
-    if (skipped(scal0, inst)) return;
-    __shared__ double v[15];
-    int qs[15];
-    int nq = 0;
-    for (int i = 0; i < C; ++i) qs[nq++] = qn + i;
-    for (int i = 0; i < C; ++i) qs[nq++] = qt + i;
-    if (qe >= 0) qs[nq++] = qe;
-    warp_sums(pa, na_tot, b * na_inst, na_inst, qs, nq, v);
-    if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)inst * S_COUNT;
-        const double M = Mb ? Mb[inst] : M0;
-        double e = (qe >= 0) ? v[2 * C] : 0.0, a = 0.0, bb = 0.0, c = 0.0, ug = 0.0, uGg = 0.0;
-        for (int i = 0; i < C; ++i) {
-            const double l = double(F - i), nl = v[i], tl = v[C + i];
-            a += nl; bb += l * nl; c += l * l * nl;
-            ug += tl; uGg += l * tl;
-        }
-        const double au = c - M * M;
-        const double al = (c * ug - M * uGg) / au;
-        const double be = (uGg - M * ug) / au;
-        if (!isfinite(c) || !isfinite(ug) || !isfinite(uGg) || !isfinite(e)) set_status(scal, SBEC_ERR_NONFINITE);
-        if (!(au > 0.0)) set_status(scal, SBEC_ERR_DOMAIN);
-        scal[slot_a] = al;
-        scal[slot_b] = be;
-        if (write_grad_info) {
-            scal[SBEC_S_ENERGY] = e;
-            scal[SBEC_S_MASS] = a;
-            scal[SBEC_S_MAG] = bb;
-            scal[S_C2] = c;
-            if (!isfinite(e) || !isfinite(al) || !isfinite(be)) set_status(scal, SBEC_ERR_NONFINITE);
-        }
-    }
-}
-
-static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, double* scal0, int slot,
-                                  const int* imap) {
-    const long long inst = inst_of(imap, blockIdx.x);
-    if (skipped(scal0, inst)) return;
-    __shared__ double v[1];
-    const int q[1] = {0};
-    warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, q, 1, v);
-    if (threadIdx.x == 0) {
-        double* scal = scal0 + (size_t)inst * S_COUNT;
-        scal[slot] = v[0];
-        if (!isfinite(v[0])) set_status(scal, SBEC_ERR_NONFINITE);
-    }
-}
-
 // Retraction scales sigma_l from m_l = |w_l|^2 (Sec. 6), one block per instance;
 // warp 0 solves, lane i holding component i, so each Newton step costs one term
 // per lane and a shuffle sum (lane 0's sum is broadcast: every lane takes the
@@ -883,21 +968,37 @@ static __global__ void k_fin_norm(const double* pa, int na_tot, int na_inst, dou
 //    h3' > 0 at the zero; bracket from t = 1 by doubling, then the same
 //    safeguarded Newton.
 //  kind 3, Lemma 5.4: closed form.
-// Both iterations stop when the step is below 4 ulps of r or after 200 steps.
+// Both iterations stop when h is at the rounding floor of its own terms
+// (|h| <= 8 eps sum |terms|: r is the zero to working precision, and further
+// steps would only move it within the noise), when the step is below 4 ulps of
+// r, or after 200 steps.
 __device__ __forceinline__ double warp_sum_bcast(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst, int F, double M0, const double* Mb,
-                                       int kind, double* scal0, const int* imap) {
-    const long long inst = inst_of(imap, blockIdx.x);
-    if (skipped(scal0, inst)) return;
+// three warp sums in one shuffle tree, every lane gets the totals
+__device__ __forceinline__ void warp_sum3_bcast(double& a, double& b, double& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    a = __shfl_sync(0xffffffffu, a, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    c = __shfl_sync(0xffffffffu, c, 0);
+}
+
+constexpr double kEps = 2.220446049250313e-16;   // 2^-52
+
+__device__ __forceinline__ void retract_solve_body(const double* pa, int na_tot, int na_inst, int F, double M0,
+                                                   const double* Mb, int kind, double* scal0, int b, long long inst) {
     __shared__ double m[7];
     const int C = 2 * F + 1;
     const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
-    warp_sums(pa, na_tot, blockIdx.x * na_inst, na_inst, qs, C, m);
+    warp_sums(pa, na_tot, b * na_inst, na_inst, qs, C, m);
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     double* scal = scal0 + (size_t)inst * S_COUNT;
@@ -927,18 +1028,20 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
             double lo = 1.0 / (f1 - M), hi = 1.0 / (f2 - M);   // h1(lo+) = -inf, h1(hi-) = +inf
             double r = 0.0;
             for (int it = 0; it < 200; ++it) {
-                double th = 0.0, tdh = 0.0;
+                double h = 0.0, dh = 0.0, habs = 0.0;
                 if (act) {
                     const double iq = 1.0 / (1.0 - d * r);
-                    th = d * ml * iq * iq;
-                    tdh = 2.0 * d * th * iq;
+                    h = d * ml * iq * iq;
+                    dh = 2.0 * d * h * iq;
+                    habs = fabs(h);
                 }
-                const double h = warp_sum_bcast(th), dh = warp_sum_bcast(tdh);
+                warp_sum3_bcast(h, dh, habs);
+                if (fabs(h) <= 8.0 * kEps * habs) break;
                 if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
                 // a Newton step below 4 ulps of r ends the iteration (tested before the
                 // bracket, which a converged step may no longer clear)
                 const double dr = (dh > 0.0) ? h / dh : 0.0;
-                if (dh > 0.0 && fabs(dr) <= 4.0 * 2.220446049250313e-16 * fmax(fabs(r), 1e-300)) {
+                if (dh > 0.0 && fabs(dr) <= 4.0 * kEps * fmax(fabs(r), 1e-300)) {
                     r -= dr;
                     break;
                 }
@@ -946,7 +1049,7 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
                 if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
                 const double step = fabs(rn - r);
                 r = rn;
-                if (step <= 4.0 * 2.220446049250313e-16 * fmax(fabs(r), 1e-300)) break;
+                if (step <= 4.0 * kEps * fmax(fabs(r), 1e-300)) break;
             }
             const double q = 1.0 - d * r;
             const double sv = warp_sum_bcast(act ? ml / (q * q) : 0.0);
@@ -955,26 +1058,30 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
             // h3(t) = sum_j (j + f1 - M) m_{f1+j} t^j, j = l - f1, over the components in [f1, f2]
             const int j = int(l - f1);
             const double cf = act ? (double(j) + f1 - M) * ml : 0.0;
-            auto h3 = [&](double t, double* dh) {
+            // h3(t), h3'(t) and sum |terms| in habs
+            auto h3 = [&](double t, double* dh, double* habs) {
                 double tp = 1.0, tpm = 0.0;          // t^j and t^(j-1)
                 for (int k = 0; k < j; ++k) { tpm = tp; tp *= t; }
-                const double v = warp_sum_bcast(act ? cf * tp : 0.0);
-                *dh = warp_sum_bcast(act && j > 0 ? double(j) * cf * tpm : 0.0);
+                double v = act ? cf * tp : 0.0;
+                *dh = act && j > 0 ? double(j) * cf * tpm : 0.0;
+                *habs = fabs(v);
+                warp_sum3_bcast(v, *dh, *habs);
                 return v;
             };
-            double dh;
+            double dh, habs;
             double lo = 0.0, hi = 1.0;
             int guard = 0;
-            if (h3(1.0, &dh) < 0.0) {
+            if (h3(1.0, &dh, &habs) < 0.0) {
                 lo = 1.0; hi = 2.0;
-                while (h3(hi, &dh) < 0.0 && guard++ < 2000) { lo = hi; hi *= 2.0; }
+                while (h3(hi, &dh, &habs) < 0.0 && guard++ < 2000) { lo = hi; hi *= 2.0; }
             }
             if (guard >= 2000) ok = false;
             double r = (lo > 0.0) ? lo : 1.0;
             for (int it = 0; it < 200 && ok; ++it) {
-                const double h = h3(r, &dh);
+                const double h = h3(r, &dh, &habs);
+                if (fabs(h) <= 8.0 * kEps * habs) break;
                 if (h < 0.0) lo = r; else if (h > 0.0) hi = r; else break;
-                if (dh > 0.0 && fabs(h / dh) <= 4.0 * 2.220446049250313e-16 * r) {
+                if (dh > 0.0 && fabs(h / dh) <= 4.0 * kEps * r) {
                     r -= h / dh;
                     break;
                 }
@@ -982,7 +1089,7 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
                 if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
                 const double step = fabs(rn - r);
                 r = rn;
-                if (step <= 4.0 * 2.220446049250313e-16 * r) break;
+                if (step <= 4.0 * kEps * r) break;
             }
             // sigma_0^2 = 1 / sum_l m_l r^l, sigma_l = sigma_0 r^{l/2}
             const int L = F - lane;
@@ -1001,6 +1108,40 @@ static __global__ void k_retract_solve(const double* pa, int na_tot, int na_inst
     if (lane < 7) scal[S_SIG + lane] = mine ? sig : 0.0;
     if (lane == 0 && !ok) set_status(scal, SBEC_ERR_DOMAIN);
 }
+
+// w = U + t Xi into out; partials m_l = |w_l|^2, from which the last block per
+// instance solves for the retraction scales sigma_l (retract_solve_body)
+template <typename T, int F>
+__global__ void __launch_bounds__(256) k_retract_w(const void* Up, const void* Xp, double t, void* Op, long long G,
+                                                   double* partials, double* scal0, int tslot, const int* imap,
+                                                   int kind, double M0, const double* Mb) {
+    using T2 = typename C2<T>::t;
+    constexpr int C = 2 * F + 1;
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long foff = inst * C * G;
+    if (tslot >= 0) t *= scal0[(size_t)inst * S_COUNT + tslot];
+    const T2* __restrict__ U = reinterpret_cast<const T2*>(Up) + foff;
+    const T2* __restrict__ Xi = reinterpret_cast<const T2*>(Xp) + foff;
+    T2* __restrict__ O = reinterpret_cast<T2*>(Op) + foff;
+    Acc<T> acc[C];
+    const T tt = T(t);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < G; p += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            T2 w = U[c * G + p];
+            caxpy(w, tt, Xi[c * G + p]);
+            acc[c].add(cabs2(w));
+            O[c * G + p] = w;
+        }
+    }
+    double v[C];
+    acc_values(acc, v);
+    block_reduce_store<C>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    if (last_block(scal0 + inst * S_COUNT, gridDim.x))
+        retract_solve_body(partials, gridDim.x * gridDim.y, gridDim.x, F, M0, Mb, kind, scal0, blockIdx.y, inst);
+}
+
 
 // ---------------------------------------------------------------------------
 // Tangent-vector BLAS-1 (Sec. 4 inner product <xi, zeta>_u = xi^T zeta on the real
@@ -1316,6 +1457,40 @@ static int elem_blocks(long long G, int num_sms, int B = 1, int per_sm = 0) {
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+// Resident 256-thread blocks per SM of a grid-stride kernel, asked once per
+// kernel (cache: a static of the call site); -1 when the runtime cannot tell.
+template <typename K>
+static int resident_256(K kern, std::atomic<int>& cache) {
+    int n = cache.load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = -1;
+        }
+        cache.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+// Grid of a grid-stride kernel over n points per instance: elem_blocks, rounded
+// down to whole waves of the kernel's resident blocks when it spans more than one
+// (8 blocks per SM over a kernel of which 6 fit would run a second, one-third-full
+// wave: 6 are launched).  Measured on the 256^3 FP32 fields: the one-third wave
+// cost the projection 25%; a kernel of which 4 fit keeps its two full waves, which
+// took 40% less time than one wave of blocks with twice the work each.
+static int elem_grid(long long n, const Geom& g, const Work& w, int resident) {
+    const int nb = elem_blocks(n, w.num_sms, g.B, g.tune.elem_per_sm);
+    if (resident <= 0) return nb;
+    const long long wave = (long long)resident * w.num_sms / (g.B > 0 ? g.B : 1);
+    if (wave < 1 || nb <= wave) return nb;
+    return (int)((nb / wave) * wave);
+}
+#define SBEC_ELEM_GRID(n, kern)                                         \
+    [&]() {                                                             \
+        static std::atomic<int> occ_{0};                                \
+        return elem_grid((n), g, w, resident_256(kern, occ_));          \
+    }()
+
 static PointParams point_params(const Geom& g) {
     PointParams pp;
     for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
@@ -1473,10 +1648,11 @@ static SArgs sargs(const Geom& g, const SCfg& c, int axis, const void* in, void*
     a.nouter = (axis == 1) ? g.n[2] : g.n[1];
     a.estride = (axis == 1) ? (long long)g.n[0] : (long long)g.n[0] * g.n[1];
     a.invG = g.invG;
-    a.partials = part; a.nblk = c.nblk;
+    a.partials = part; a.nblk = c.nblk; a.nblk_inst = c.nblk_inst;
     a.C = g.C;
     a.skip = g.skip;
     a.imap = g.imap;
+    a.fe = FinEnergy{};
     return a;
 }
 
@@ -1492,7 +1668,20 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.ppb = reinterpret_cast<const PointParams*>(g.ppb);
     a.skip = g.skip;
     a.imap = g.imap;
+    a.fp = FinProj{};
+    a.fe = 0;
     return a;
+}
+
+// Lemma 4.1 finalize run by the producer's last block per instance
+static FinProj fin_proj(const Geom& g, const Work& w, int qe, int qn, int qt, int slot_a, int slot_b,
+                        int write_grad_info) {
+    FinProj f;
+    f.on = 1;
+    f.qe = qe; f.qn = qn; f.qt = qt;
+    f.slot_a = slot_a; f.slot_b = slot_b; f.write_grad_info = write_grad_info;
+    f.M0 = g.M; f.Mb = g.Mb; f.scal0 = w.scal;
+    return f;
 }
 
 // Forward transforms of every axis but x after the x pass, then the fused
@@ -1522,9 +1711,13 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
     if ((size_t)c.nblk * (1 + 2 * C) > w.part_cap) return SBEC_ERR_ARG;
     void* gout = Geuc ? Geuc : ((Griem || want_norm) ? w.work2 : nullptr);
     int st;
+    // the Lemma 4.1 coefficients alpha_g, beta_g and E, mass, magnetisation: finalized
+    // by the last block per instance of the pass that stores the partials
+    const FinProj fg = fin_proj(g, w, 0, 1, 1 + C, SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1);
     if (g.dim == 1) {
         XArgs a = xargs<T>(g, c, X, gout, w.partA);
         a.X = X;
+        a.fp = fg;
         st = launch_x<T, F, X_FULL_GRAD>(c, a, w, s);
         if (st) return st;
     } else {
@@ -1541,19 +1734,14 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
         XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
         a.X = X;
+        a.fp = fg;
         st = launch_epi<T, F, false>(g, w, a, ne, s);
         if (st) return st;
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                    SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
     }
-    if (g.dim == 1)
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, 0, 1, 1 + C, g.M, g.Mb, w.scal,
-                    SBEC_S_ALPHA_G, SBEC_S_BETA_G, 1, g.imap);
     if (Griem || want_norm) {
-        const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, gout, Griem, g.G, w.scal, SBEC_S_ALPHA_G,
-                    SBEC_S_BETA_G, w.partB, g.imap);
-        SBEC_LAUNCH(K_FIN, k_fin_norm, g.nl, 256, w.partB, nb * g.nl, nb, w.scal, SBEC_S_RGRAD_NORM2, g.imap);
+        const int nb = SBEC_ELEM_GRID(g.G, (k_proj_apply<T, F, true>));
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F, true>), dim3(nb, g.nl), 256, X, gout, Griem, g.G, w.scal,
+                    SBEC_S_ALPHA_G, SBEC_S_BETA_G, w.partB, g.imap, SBEC_S_RGRAD_NORM2);
     }
     return SBEC_OK;
 }
@@ -1562,44 +1750,43 @@ template <typename T, int F>
 static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s) {
     const XCfg c = xcfg<T>(g);
     int st;
+    // E (Eq. 3.7) finalized by the last block per instance of the last pass
     if (g.dim == 1) {
-        st = launch_x<T, F, X_FULL_ENERGY>(c, xargs<T>(g, c, X, nullptr, w.partA), w, s);
-        if (st) return st;
-        SBEC_LAUNCH(K_FIN, k_fin_energy, g.nl, 256, w.partA, c.nblk, c.nblk_inst, 2, nullptr, 0, 0, w.scal, g.imap);
-        return SBEC_OK;
+        XArgs a = xargs<T>(g, c, X, nullptr, w.partA);
+        a.fe = 1;
+        a.fp.scal0 = w.scal;
+        return launch_x<T, F, X_FULL_ENERGY>(c, a, w, s);
     }
     st = launch_x<T, F, X_FWD_EPW>(c, xargs<T>(g, c, X, w.work, w.partA), w, s);
     if (st) return st;
-    SCfg cl;
-    if (g.dim == 2) {
-        cl = scfg<T>(g, 1, w.num_sms);
-        st = launch_s<T, S_PARSEVAL>(cl, sargs<T>(g, cl, 1, w.work, nullptr, w.partB), w, s);
-    } else {
+    const int axis = g.dim == 2 ? 1 : 2;
+    if (g.dim == 3) {
         const SCfg cy = scfg<T>(g, 1, w.num_sms);
-        cl = scfg<T>(g, 2, w.num_sms);
         st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
         if (st) return st;
-        st = launch_s<T, S_PARSEVAL>(cl, sargs<T>(g, cl, 2, w.work, nullptr, w.partB), w, s);
     }
-    if (st) return st;
-    SBEC_LAUNCH(K_FIN, k_fin_energy, g.nl, 256, w.partA, c.nblk, c.nblk_inst, 1, w.partB, cl.nblk, cl.nblk_inst,
-                w.scal, g.imap);
-    return SBEC_OK;
+    const SCfg cl = scfg<T>(g, axis, w.num_sms);
+    SArgs a = sargs<T>(g, cl, axis, w.work, nullptr, w.partB);
+    a.fe.on = 1;
+    a.fe.pa = w.partA; a.fe.na_tot = c.nblk; a.fe.na_inst = c.nblk_inst;
+    a.fe.scal0 = w.scal;
+    return launch_s<T, S_PARSEVAL>(cl, a, w, s);
 }
 
 template <typename T, int F>
 static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
                   cudaStream_t s, int sigslot = -1) {
     constexpr int C = 2 * F + 1;
-    const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
+    const int nb = SBEC_ELEM_GRID(g.G, (k_proj_apply<T, F, false>));
     const void* zin = Z;
+    // P_u coefficients (Lemma 4.1) into S_PA, S_PB by the last block per instance
+    const FinProj fpz = fin_proj(g, w, -1, 0, C, S_PA, S_PB, 0);
     if (riem) {
         // xi = P_u Z (Lemma 4.1)
-        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nb, g.nl), 256, X, Z, g.G, w.partB, w.scal, g.imap);
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partB, nb * g.nl, nb, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA, S_PB,
-                    0, g.imap);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, Z, w.work2, g.G, w.scal, S_PA, S_PB,
-                    w.partB, g.imap);
+        const int nd = SBEC_ELEM_GRID(g.G, (k_dot_reduce<T, F>));
+        SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nd, g.nl), 256, X, Z, g.G, w.partB, w.scal, g.imap, fpz);
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F, false>), dim3(nb, g.nl), 256, X, Z, w.work2, g.G, w.scal, S_PA,
+                    S_PB, nullptr, g.imap, -1);
         zin = w.work2;
     }
     const XCfg c = xcfg<T>(g);
@@ -1609,6 +1796,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
     if (g.dim == 1) {
         XArgs a = xargs<T>(g, c, zin, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
+        if (riem) a.fp = fpz;
         st = launch_x<T, F, X_FULL_HESS>(c, a, w, s);
         if (st) return st;
     } else {
@@ -1618,35 +1806,30 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         if (st) return st;
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
+        if (riem) a.fp = fpz;
         // inverse x-FFT in place, then the Hessian epilogue (split as in grad_F)
         st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
         if (st) return st;
         const int ne = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
         st = launch_epi<T, F, true>(g, w, a, ne, s);
         if (st) return st;
-        if (riem) {
-            SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, -1, 0, C, g.M, g.Mb, w.scal,
-                        S_PA, S_PB, 0, g.imap);
-            SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
-                        w.partB, g.imap);
-        }
-        return SBEC_OK;
+        if (riem && !EpiFusedFin<T, F, true>::v)
+            SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, ne * g.nl, ne, F, fpz, g.imap);
     }
-    if (riem) {
-        SBEC_LAUNCH(K_FIN, k_fin_proj, g.nl, 256, w.partA, c.nblk, c.nblk_inst, F, -1, 0, C, g.M, g.Mb, w.scal, S_PA,
-                    S_PB, 0, g.imap);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB, w.partB, g.imap);
-    }
+    if (riem)
+        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F, false>), dim3(nb, g.nl), 256, X, HZ, HZ, g.G, w.scal, S_PA, S_PB,
+                    nullptr, g.imap, -1);
     return SBEC_OK;
 }
 
 template <typename T, int F>
 static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind, void* out,
                      cudaStream_t s, int tslot = -1) {
-    const int nb = elem_blocks(g.G, w.num_sms, g.B, g.tune.elem_per_sm);
-    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.nl), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot, g.imap);
-    SBEC_LAUNCH(K_RSOLVE, k_retract_solve, g.nl, 256, w.partB, nb * g.nl, nb, F, g.M, g.Mb, kind, w.scal, g.imap);
-    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(nb, g.nl), 256, out, g.G, w.scal, g.imap);
+    const int nb = SBEC_ELEM_GRID(g.G, (k_retract_w<T, F>));
+    const int ns = SBEC_ELEM_GRID(g.G, (k_scale<T, F>));
+    SBEC_LAUNCH(K_RETW, (k_retract_w<T, F>), dim3(nb, g.nl), 256, U, Xi, t, out, g.G, w.partB, w.scal, tslot, g.imap,
+                kind, g.M, g.Mb);
+    SBEC_LAUNCH(K_SCALE, (k_scale<T, F>), dim3(ns, g.nl), 256, out, g.G, w.scal, g.imap);
     return SBEC_OK;
 }
 
@@ -1692,7 +1875,7 @@ int Ops<T>::retract(const Geom& g, const Work& w, const void* U, const void* Xi,
 template <typename T>
 int Ops<T>::lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
+    const int nb = SBEC_ELEM_GRID(N / 2, k_lincomb<T>);
     const bool dots = (L.D1 || L.D2);
     SBEC_LAUNCH(K_LIN, k_lincomb<T>, dim3(nb, g.nl), 256, L, N, w.scal, dots ? w.partB : nullptr, g.imap);
     if (dots) SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, 2, w.scal, dot_slot, g.imap);
@@ -1703,7 +1886,7 @@ template <typename T>
 int Ops<T>::dot2(const Geom& g, const Work& w, const void* A, const void* B, const void* C, const void* D, int slot,
                  cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
+    const int nb = SBEC_ELEM_GRID(N / 2, k_dot2<T>);
     SBEC_LAUNCH(K_DOT, k_dot2<T>, dim3(nb, g.nl), 256, A, B, C, D, N, w.partB, w.scal, g.imap);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, C ? 2 : 1, w.scal, slot, g.imap);
     return SBEC_OK;
@@ -1713,7 +1896,7 @@ template <typename T>
 int Ops<T>::bbdots(const Geom& g, const Work& w, const void* U, const void* UP, const void* Gv, const void* GP,
                    int slot, cudaStream_t s) {
     const long long N = 2LL * g.C * g.G;
-    const int nb = elem_blocks(N / 2, w.num_sms, g.B, g.tune.elem_per_sm);
+    const int nb = SBEC_ELEM_GRID(N / 2, k_bbdots<T>);
     SBEC_LAUNCH(K_DOT, k_bbdots<T>, dim3(nb, g.nl), 256, U, UP, Gv, GP, N, w.partB, w.scal, g.imap);
     SBEC_LAUNCH(K_FIN, k_fin_sums, g.nl, 256, w.partB, nb * g.nl, nb, 2, w.scal, slot, g.imap);
     return SBEC_OK;

@@ -66,7 +66,7 @@ enum {
     SL_CGNEG = SL_D0 + 27,        // CG ended at its first iteration on curvature: xi = -grad
     SL_CGHD = SL_D0 + 28,         // CG ended later on negative curvature: xi = s + tau d
 };
-static_assert(SL_CGHD < sbec::S_COUNT, "solver slots exceed the scalar block");
+static_assert(int(SL_CGHD) < int(sbec::S_COUNT), "solver slots exceed the scalar block");
 
 // S_SKIP value of an instance whose modified CG has ended inside a chunk
 constexpr double kSkipCg = 2.0;
