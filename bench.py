@@ -260,8 +260,8 @@ def bytes_model(w, kname, elem, B=1):
 
 
 def roofline_of(prof, w, precision, B, wname):
-    # the dominant kernel among those with an algorithmic model (the scalar finalize and
-    # retraction-solve kernels have none: they are launch-latency work)
+    # the dominant kernel among those with an algorithmic model (the one-block finalize
+    # kernels have none: they are launch-latency work)
     total = sum(v[0] for v in prof.values())
     modelled = {k: v for k, v in prof.items()
                 if (flops_model(w, k, B) if precision == "fp64" else bytes_model(w, k, 8, B))}

@@ -369,7 +369,7 @@ long long sbec_launch_count(const sbec_handle* h) { return h ? h->prof.launches 
 static const char* kKernelNames[sbec::K_COUNT] = {
     "x_fwd", "x_fwd_energy", "x_inv_grad", "x_inv_hess", "x_full_grad", "x_full_energy", "x_full_hess",
     "s_fwd", "s_inv", "s_k2", "s_parseval", "dot_reduce", "proj_apply", "retract_w", "scale", "finalize",
-    "retract_solve", "tables", "lincomb", "prolong", "x_inv"};
+    "tables", "lincomb", "prolong", "x_inv"};
 
 int sbec_profile(sbec_handle* h, int enable) {
     if (!h) return SBEC_ERR_ARG;

@@ -69,7 +69,7 @@ struct Geom {
 // Kernel identities for the per-kernel launch counter and event timer.
 enum KernelId {
     K_X_FWD, K_X_FWD_EPW, K_X_INV_GRAD, K_X_INV_HESS, K_X_FULL_GRAD, K_X_FULL_ENERGY, K_X_FULL_HESS,
-    K_S_FWD, K_S_INV, K_S_K2, K_S_PARSEVAL, K_DOT, K_PROJ, K_RETW, K_SCALE, K_FIN, K_RSOLVE, K_TABLES,
+    K_S_FWD, K_S_INV, K_S_K2, K_S_PARSEVAL, K_DOT, K_PROJ, K_RETW, K_SCALE, K_FIN, K_TABLES,
     K_LIN, K_PROLONG, K_X_INV, K_COUNT
 };
 
