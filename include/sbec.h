@@ -216,7 +216,8 @@ const double* sbec_scalars(const sbec_handle* h);
  * shared-memory tile of the FFT pass along axis a, a power of 2 <= n[0];
  * s_split[a]: butterflies per thread of that pass (1, 2, 4 or 8).
  * elem_per_sm: blocks per SM of the grid-stride elementwise and reduction
- * kernels (1..32).  At most 16384 points per FFT block and 227 KB of shared
+ * kernels (1..32); a kernel of which fewer blocks fit per SM gets whole waves
+ * of the blocks that fit.  At most 16384 points per FFT block and 227 KB of shared
  * memory.  [0] entries and the entries of axes >= dim are 0.  In
  * sbec_set_tune a 0 field keeps the built-in choice. */
 typedef struct sbec_tune {
