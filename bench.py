@@ -239,14 +239,16 @@ def flops_model(w, kname, B=1):
     if kname in ("s_fwd", "s_inv", "s_parseval") and d > 1:
         m = n[1] if kname != "s_parseval" else n[-1]
         return B * C * (G // m) * fft(m)
-    if kname == "x_fwd":
+    if kname in ("x_fwd", "x_inv"):
         return B * C * (G // n[0]) * fft(n[0])
     if kname == "x_fwd_energy":
         return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["energy"][w.F])
+    # 2D/3D: the gradient and Hessian epilogues are pointwise kernels of their own
+    # (the inverse x transform before them is the x_inv launch)
     if kname == "x_inv_grad":
-        return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["grad"][w.F])
+        return B * G * PW_FLOPS["grad"][w.F]
     if kname == "x_inv_hess":
-        return B * (C * (G // n[0]) * fft(n[0]) + G * PW_FLOPS["hess"][w.F])
+        return B * G * PW_FLOPS["hess"][w.F]
     if kname == "x_full_grad":
         return B * (C * (2 * fft(n[0]) + 4 * n[0]) + G * PW_FLOPS["grad"][w.F])
     if kname == "x_full_hess":
@@ -259,7 +261,7 @@ def bytes_model(w, kname, elem, B=1):
     C, G = w.C, int(np.prod(w.n))
     S = B * C * G * elem
     SV = B * G * elem // 2
-    return {"x_fwd": 2 * S, "x_fwd_energy": 2 * S + SV, "s_k2": 2 * S, "s_fwd": 2 * S, "s_inv": 2 * S,
+    return {"x_fwd": 2 * S, "x_inv": 2 * S, "x_fwd_energy": 2 * S + SV, "s_k2": 2 * S, "s_fwd": 2 * S, "s_inv": 2 * S,
             "s_parseval": S, "x_inv_grad": 3 * S + SV, "x_inv_hess": 4 * S + SV, "x_full_grad": 3 * S + SV,
             "x_full_hess": 4 * S + SV, "proj_apply": 3 * S, "dot_reduce": 2 * S, "retract_w": 3 * S,
             "scale": 2 * S, "lincomb": 3 * S}.get(kname)

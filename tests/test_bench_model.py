@@ -1,0 +1,66 @@
+"""The bench's algorithmic work model (roofline numerators) against the counts
+the design states: a length-m complex FFT is 5 m log2 m flops; the last-axis
+pass is a forward and an inverse transform plus the |k|^2/G scaling (4 flops per
+element); the 2D/3D gradient and Hessian epilogues are pointwise kernels of
+their own (the inverse x transform before them is a separate launch), so their
+flops are the per-point counts only; DRAM bytes are the compulsory reads and
+writes of each launch in units of one field S and of the potential S_V."""
+import math
+
+import pytest
+
+import bench
+from paper_1907_01194_gb300 import workloads as W
+
+
+def _fft(m):
+    return 5.0 * m * math.log2(m)
+
+
+@pytest.mark.parametrize("name", ["spin2_2d", "spin3_3d_128", "spin3_3d_256"])
+def test_flop_model(name):
+    w = bench.workload(name)
+    C, n = w.C, w.n
+    G = math.prod(n)
+    rows_x = G // n[0]
+    assert bench.flops_model(w, "x_fwd") == C * rows_x * _fft(n[0])
+    assert bench.flops_model(w, "x_inv") == C * rows_x * _fft(n[0])
+    assert bench.flops_model(w, "x_fwd_energy") == C * rows_x * _fft(n[0]) + G * bench.PW_FLOPS["energy"][w.F]
+    # epilogues: pointwise only
+    assert bench.flops_model(w, "x_inv_grad") == G * bench.PW_FLOPS["grad"][w.F]
+    assert bench.flops_model(w, "x_inv_hess") == G * bench.PW_FLOPS["hess"][w.F]
+    m = n[-1]
+    assert bench.flops_model(w, "s_k2") == C * (G // m) * (2 * _fft(m) + 4 * m)
+    # batches scale linearly
+    assert bench.flops_model(w, "x_inv_hess", 3) == 3 * bench.flops_model(w, "x_inv_hess")
+
+
+def test_flop_model_1d_full_passes():
+    w = W.spin1_1d()
+    n, C, G = w.n[0], w.C, w.n[0]
+    assert bench.flops_model(w, "x_full_grad") == C * (2 * _fft(n) + 4 * n) + G * bench.PW_FLOPS["grad"][1]
+    assert bench.flops_model(w, "x_full_hess") == C * (2 * _fft(n) + 4 * n) + G * bench.PW_FLOPS["hess"][1]
+
+
+@pytest.mark.parametrize("elem", [8, 16])
+def test_byte_model(elem):
+    w = bench.workload("spin3_3d_256")
+    G = math.prod(w.n)
+    S = w.C * G * elem
+    SV = G * elem // 2
+    expect = {"x_fwd": 2 * S, "x_inv": 2 * S, "x_fwd_energy": 2 * S + SV, "s_fwd": 2 * S, "s_inv": 2 * S,
+              "s_k2": 2 * S, "s_parseval": S, "x_inv_grad": 3 * S + SV, "x_inv_hess": 4 * S + SV,
+              "proj_apply": 3 * S, "dot_reduce": 2 * S, "retract_w": 3 * S, "scale": 2 * S, "lincomb": 3 * S}
+    for k, v in expect.items():
+        assert bench.bytes_model(w, k, elem) == v, k
+    assert bench.bytes_model(w, "finalize", elem) is None
+
+
+def test_roofline_picks_the_longest_modelled_kernel():
+    w = bench.workload("spin3_3d_128")
+    prof = {"x_inv_hess": (4.0, 1), "s_k2": (2.5, 2), "finalize": (9.0, 3)}
+    r = bench.roofline_of(prof, w, "fp64", 1, w.name)
+    assert r["kernel"] == "x_inv_hess" and r["bound"] == "alu"
+    fl = math.prod(w.n) * bench.PW_FLOPS["hess"][w.F]
+    assert r["achieved"] == pytest.approx(fl / 4.0e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_GFLOPS)
