@@ -142,6 +142,12 @@ typedef struct sbec_solve_opts {
     int    cuda_graphs;      /* 1 (default): every CG chunk is the replay of a CUDA graph
                                 captured once per solve; 0: its kernels are launched one
                                 by one.  Graphs are not used while sbec_profile is on */
+    int    refine_cg_fp32;   /* sbec_solve_mixed on single handles: 1 (default): in the FP64
+                                refinement the modified CG runs on the SBEC_MIXED handle
+                                (FP32 Hessian-vector products at u rounded to float), while
+                                the gradient, energy, model value, search, retraction and
+                                the stopping test stay FP64; 0: every step in FP64.
+                                Ignored by the other solvers */
 } sbec_solve_opts;
 
 typedef struct sbec_stats {
@@ -155,7 +161,8 @@ typedef struct sbec_stats {
 } sbec_stats;
 
 /* Paper defaults: ARNT with R1, tol 1e-6, maxit 10000, RGBB warm start to 1e-2
- * or 2000 iterations, project_initial 1; cg_chunk 4, cuda_graphs 1. */
+ * or 2000 iterations, project_initial 1; cg_chunk 4, cuda_graphs 1,
+ * refine_cg_fp32 1. */
 void sbec_solve_defaults(sbec_solve_opts* opts);
 
 /* Bytes of device workspace sbec_solve needs for the handle's problem (ten fields). */
@@ -201,6 +208,17 @@ int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_sol
 int sbec_prolongate(sbec_handle* hc, const void* Xc, sbec_handle* hf, void* Xf);
 int sbec_solve_cascadic(sbec_handle* const* levels, int nlevels, void* const* X, const sbec_solve_opts* opts,
                         double tol_coarse, void* workspace, size_t workspace_bytes, sbec_stats* stats);
+
+/* sbec_solve_cascadic with the mixed form on every level: levels64[j] (SBEC_FP64)
+ * and levels32[j] (SBEC_MIXED) describe level j; each level runs
+ * sbec_solve_mixed (tolerance max(tol_coarse, opts->tol) on coarse levels,
+ * opts->tol on the finest) and its FP64 result is prolongated with
+ * sbec_prolongate on the FP64 handles.  X[j]: complex128 device arrays.
+ * workspace: at least sbec_solve_mixed_workspace_bytes of the finest pair.
+ * Stats are those of the finest level's two phases. */
+int sbec_solve_cascadic_mixed(sbec_handle* const* levels64, sbec_handle* const* levels32, int nlevels,
+                              void* const* X, const sbec_solve_opts* opts, double tol_coarse, double tol_mixed,
+                              void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64);
 
 /* Stream synchronisation; returns the first device-side error recorded since
  * the previous sbec_sync (and clears it), or SBEC_ERR_CUDA. */
@@ -258,25 +276,37 @@ long long sbec_launch_count(const sbec_handle* h);
 int sbec_profile(sbec_handle* h, int enable);
 int sbec_profile_read(sbec_handle* h, int max, char* names, double* ms, long long* counts, int* rows);
 
-/* Allocation-free energy (the paper has no counterpart: this is a service of
- * the library).  For callers that must not allocate device memory when they
- * need the energy, for example a host framework that owns all device memory
- * through its own pool, or a latency-critical loop that cannot afford
- * cudaMalloc/cudaFree (which can wait for the whole device to go idle).
- * Computes E_h(X) (Eq. 3.7) like sbec_energy but without a handle: every
- * intermediate lives in one fixed 8 MiB array of device memory inside the
- * library image, which each GPU that loads the library holds until the process
- * exits.  prob must have precision SBEC_FP64; V is a device array of G doubles
- * or NULL for the harmonic trap; X is a device array in the state layout; E is
- * a host pointer; the call runs on cuda_stream and synchronises it.  The array
- * holds 2^20 doubles: the transformed field (2 C G doubles), the harmonic
- * potential when V is NULL (G), and about 40,000 doubles of tables and partial
- * sums; a problem that needs more is rejected with SBEC_ERR_ARG (spin-3 on
- * 256 x 256 fits, spin-3 on 512 x 256 does not).  The first call on a device looks up the
- * array's device address, so make it before any stream capture.  All calls
- * share the one array and leave their intermediates in it: calls that overlap
- * on the GPU (other streams or host threads) race and must be serialised by
- * the caller. */
+/* Arithmetic peak probe (not in the paper: instrumentation of this library).
+ * Runs independent chains of fused multiply-adds in double (precision
+ * SBEC_FP64) or float (SBEC_MIXED) on every SM of the current device, `iters`
+ * steps per chain, on a private stream; *gflops receives the best of three
+ * timed launches in GFLOP/s (2 per FMA).  The FP64 form of the hot path is
+ * bound by this rate rather than by HBM bandwidth; it is the denominator of
+ * its roofline.  Synchronises its stream; allocates nothing. */
+int sbec_probe_fma_peak(int precision, int iters, double* gflops);
+
+/* Allocation-free energy.  The paper has no counterpart: this is a service
+ * of the library, not a step of the method.  It is for callers that must not
+ * allocate device memory when they need the energy, for example a host
+ * framework that owns all device memory through its own pool, or a
+ * latency-critical loop that cannot afford cudaMalloc/cudaFree (which can
+ * wait for the whole device to go idle).  It returns the same energy as
+ * sbec_energy but needs no handle: every intermediate lives in one fixed
+ * 8 MiB array of device memory inside the library image, which each GPU that
+ * loads the library holds until the process exits.  prob must have precision
+ * SBEC_FP64.  X (the state layout) and V (G doubles, or NULL for the harmonic
+ * trap) must be device (or managed) memory of the current device: they are
+ * read in place, and any other pointer is rejected with SBEC_ERR_ARG.  E is a
+ * host pointer; the call runs on cuda_stream, synchronises it and reads E
+ * back before returning.  The array holds 2^20 doubles: the transformed field
+ * (2 C G doubles), the harmonic potential when V is NULL (G), and about
+ * 40,000 doubles of tables and partial sums; a problem that needs more is
+ * rejected with SBEC_ERR_ARG (spin-3 on 256 x 256 fits, spin-3 on 512 x 256
+ * does not).  The first call on a device looks up the array's device
+ * address, so make it before any stream capture.  All calls share the one
+ * array and leave their intermediates in it: calls that overlap on the GPU
+ * (other streams or host threads) race and must be serialised by the
+ * caller. */
 int sbec_energy_noalloc(const sbec_problem* prob, const double* V, const void* X, double* E,
                         void* cuda_stream);
 

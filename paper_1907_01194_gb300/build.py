@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsbec.so")
 
 SOURCES = ["sbec_capi.cu", "sbec_kernels_f64.cu", "sbec_kernels_f32.cu", "sbec_noalloc.cu", "sbec_solver.cu",
-           "sbec_tune.cu"]
+           "sbec_tune.cu", "sbec_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, "-I", CSRC]

@@ -11,6 +11,8 @@
 // image, so it needs no handle and allocates nothing.
 #include <math.h>
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "sbec.h"
@@ -25,8 +27,10 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 // Device address of g_noalloc_scratch per device ordinal; in host code the
 // array's name only stands in for the symbol, it is not a device address.
+// Atomic entries: host threads may make their first calls concurrently (they
+// would store the same address, but plain stores would still race).
 constexpr int kMaxDevices = 64;
-static double* g_scratch_addr[kMaxDevices];
+static std::atomic<double*> g_scratch_addr[kMaxDevices];
 
 // lambda_p^2 = (2 pi p / (b - a))^2 per axis, p the signed DFT frequency (Eq. 3.6);
 // unused axes (n = 1) get 0.
@@ -52,16 +56,33 @@ int scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return SBEC_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) return SBEC_ERR_ARG;
-    if (!g_scratch_addr[dev]) {
+    double* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return SBEC_ERR_CUDA;
         }
-        g_scratch_addr[dev] = static_cast<double*>(p);
+        addr = static_cast<double*>(p);
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = addr;
     return SBEC_OK;
+}
+
+// p is memory of the current device that kernels may read: device or managed
+// memory of device `dev`.  The kernels of this entry point read X and V in place
+// (there is no staging area to copy host arrays into), so a host or peer-device
+// pointer is rejected here instead of being dereferenced on the GPU.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    if (at.type == cudaMemoryTypeManaged) return at.device == dev || at.device < 0;
+    return false;
 }
 
 }  // namespace
@@ -85,6 +106,7 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
     if (int st = scratch_for_current_device(&base)) return st;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
+    if (!on_device(X, dev) || (V && !on_device(V, dev))) return SBEC_ERR_ARG;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
     // geometry and parameters of the problem (Sec. 3 with h -> dV)
@@ -124,6 +146,9 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
     const size_t o_sc = off;   off += up256(sbec::S_COUNT);
     if (off > kScratchDoubles) return SBEC_ERR_ARG;   // problem too large for the fixed 8 MiB array
 
+    // Only FP64 reaches the kernels here: their FP64 branches read lam2 and invG,
+    // never the lambda^2 / G tables of the FP32 passes (g.k2s), which this entry
+    // point does not build and leaves null.
     sbec::Work w = {};
     w.work = base + o_work;
     w.work2 = nullptr;

@@ -103,6 +103,19 @@ __global__ void k_cg_ctl(double* scal0, int nl, const int* imap, int rr_now, int
     }
 }
 
+// elementwise precision change of n reals
+template <typename TS, typename TD>
+__global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = TD(src[i]);
+}
+
+template <typename TS, typename TD>
+int cast_field(const void* src, void* dst, long long nreal, int num_sms, cudaStream_t s) {
+    k_cast<TS, TD><<<4 * num_sms, 256, 0, s>>>(static_cast<const TS*>(src), static_cast<TD*>(dst), nreal);
+    return cudaGetLastError() == cudaSuccess ? SBEC_OK : SBEC_ERR_CUDA;
+}
+
 // S_SKIP of every instance back to 0
 __global__ void k_unskip(double* scal0, int B) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,6 +219,17 @@ struct CgChunks {
     }
 };
 
+// FP32 context of the modified CG inside an FP64 solve (the refinement phase of
+// sbec_solve_mixed): the Newton systems of ARNT are solved with Hessian-vector
+// products of the mixed handle of the same problem at u rounded to float, while
+// the gradient, the energy, the model value m_k, the search and the retraction
+// stay in FP64.  The CG only has to produce a descent direction of the model;
+// the stopping test on ||grad E|| is always taken in FP64.
+struct InnerCg {
+    sbec_handle* h = nullptr;      // SBEC_MIXED handle (same problem and stream)
+    void* f[6] = {};               // float fields: u, rg, x, r, p, Hp
+};
+
 constexpr double kEps = 2.220446049250313e-16;
 
 template <typename T>
@@ -219,12 +243,19 @@ struct Solver {
     void* f[10];
     int status = SBEC_OK;
     CgChunks<T> cgc;
+    const InnerCg* in;
+    CgChunks<float>* cg32 = nullptr;
 
-    Solver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt)
-        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), cgc(hh, oo.cg_chunk, oo.cuda_graphs != 0) {
+    Solver(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, sbec_stats* stt, const InnerCg* inner = nullptr)
+        : h(hh), g(hh->geom), w(hh->work), s(hh->stream), o(oo), st(stt), cgc(hh, oo.cg_chunk, oo.cuda_graphs != 0),
+          in(inner && inner->h && sizeof(T) == 8 ? inner : nullptr) {
         char* b = static_cast<char*>(ws);
         for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
+        if (in) cg32 = new CgChunks<float>(in->h, oo.cg_chunk, oo.cuda_graphs != 0);
     }
+    ~Solver() { delete cg32; }
+    Solver(const Solver&) = delete;
+    Solver& operator=(const Solver&) = delete;
 
     // scalars of the block after the launched work; returns the device status
     int pull() { return sbec_read_scalars(h); }
@@ -311,6 +342,84 @@ struct Solver {
         return SBEC_OK;
     }
 
+    // Modified CG of one ARNT iteration on the FP32 handle of the inner context:
+    // u and grad are rounded to float, the Lemma 4.2 coefficients of the FP64
+    // gradient at u are copied into the float handle's scalar block, and the same
+    // device-driven chunks as the FP64 path run there.  On return x (FP64) holds
+    // the direction s + tau d of Eq. (xi), unless the CG ended at its first
+    // iteration on curvature (s_is_neg_rg: the caller takes -grad).
+    int cg_fp32(const void* u, const void* rg, void* x, double sigma, double stop, int max_inner, bool& s_is_neg_rg,
+                double& sig_est) {
+        if constexpr (sizeof(T) != 8) {
+            return SBEC_ERR_ARG;
+        } else {
+            sbec_handle* h32 = in->h;
+            const sbec::Geom& g32 = h32->geom;
+            const sbec::Work& w32 = h32->work;
+            void *u32 = in->f[0], *rg32 = in->f[1], *x32 = in->f[2], *r32 = in->f[3], *p32 = in->f[4],
+                 *Hp32 = in->f[5];
+            const long long nreal = 2LL * g.C * g.G;
+            TRY((cast_field<double, float>(u, u32, nreal, w.num_sms, s)));
+            TRY((cast_field<double, float>(rg, rg32, nreal, w.num_sms, s)));
+            if (cudaMemcpyAsync(w32.scal + SBEC_S_ALPHA_G, w.scal + SBEC_S_ALPHA_G, 2 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return SBEC_ERR_CUDA;
+            auto lin32 = [&](void* out, double ca, const void* A, double cb, const void* B, int ib, int guard,
+                             const void* D1, int slot) {
+                Lin L;
+                L.out = out; L.A = A; L.B = B; L.ca = ca; L.cb = cb; L.ia = -1; L.ib = ib; L.ineg = -1;
+                L.D1 = D1; L.D2 = nullptr; L.guard = guard;
+                return Ops<float>::lincomb(g32, w32, L, slot, s);
+            };
+            TRY(lin32(x32, 0.0, rg32, 0.0, nullptr, -1, -1, nullptr, SL_D0));
+            TRY(lin32(r32, -1.0, rg32, 0.0, nullptr, -1, -1, r32, SL_RRA));
+            TRY(lin32(p32, 1.0, r32, 0.0, nullptr, -1, -1, nullptr, SL_D0));
+            int ds = sbec_read_scalars(h32);
+            if (ds) return ds;
+            double* q = h32->h_scal;
+            if (!(q[SL_RRA] > 0.0)) return SBEC_OK;          // grad rounds to 0 in float: x = 0
+            q[SL_SIG] = sigma; q[SL_STOP] = stop; q[SL_MAXIN] = (double)max_inner;
+            q[SL_J] = 0.0; q[SL_CG] = 1.0; q[SL_SEST] = -1.0; q[SL_CGNEG] = 0.0; q[SL_CGHD] = 0.0;
+            q[sbec::S_SKIP] = 0.0;
+            auto push32 = [&]() {
+                return cudaMemcpyAsync(w32.scal, h32->h_scal, sbec::S_COUNT * sizeof(double), cudaMemcpyHostToDevice,
+                                       s) == cudaSuccess
+                           ? SBEC_OK
+                           : SBEC_ERR_CUDA;
+            };
+            TRY(push32());
+            long long done_its = 0;
+            while (true) {
+                TRY(cg32->run(u32, p32, Hp32, x32, r32, (int)(done_its & 1)));
+                done_its += cg32->K;
+                ds = sbec_read_scalars(h32);
+                if (ds) return ds;
+                if (q[SL_CG] == 0.0) break;
+                if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+            }
+            const long long its = (long long)q[SL_J];
+            st->inner_iters += its;
+            st->n_hvp += its;
+            sig_est = q[SL_SEST];
+            const bool neg = q[SL_CGNEG] != 0.0, hd = q[SL_CGHD] != 0.0;
+            q[sbec::S_SKIP] = 0.0;
+            TRY(push32());
+            if (neg) {
+                s_is_neg_rg = true;
+                return SBEC_OK;
+            }
+            double tau = 0.0;
+            if (hd) {
+                TRY(Ops<float>::dot2(g32, w32, p32, rg32, p32, Hp32, SL_D0, s));
+                ds = sbec_read_scalars(h32);
+                if (ds) return ds;
+                tau = q[SL_D0] / q[SL_D0 + 1];
+                TRY(lin32(x32, 1.0, x32, tau, p32, -1, -1, nullptr, SL_D0));
+            }
+            return cast_field<float, double>(x32, x, nreal, w.num_sms, s);
+        }
+    }
+
     // ARNT from u (Algorithm 1, second loop)
     int arnt(void*& u, void*& z, void* gE, void* rg, void* x, void* r, void* p, void* Hp, double tol,
              long long maxit, double& E, double& gn) {
@@ -327,15 +436,21 @@ struct Solver {
             const double sigma = fmax(sig_hat * gn, sig_floor);
             const int max_inner = gn > 1e-3 ? 100 : 300;
             // ---- modified CG on Hess m_k [xi] = -grad m_k (Eq. prob-lsub) ----
-            TRY(lin(x, 0.0, rg, 0.0, nullptr));
-            TRY(lin(r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
-            TRY(lin(p, 1.0, r, 0.0, nullptr));
-            PULL(ds);
-            double rr = sc(SL_RRA);
             const double stop = fmin(0.1, gn) * gn;
             bool s_is_neg_rg = false, have_d = false;
             double sig_est = -1.0;
-            if (rr > 0.0) {
+            double rr = 0.0;
+            if (in) {
+                // the Newton system in FP32 on the mixed handle; x receives s + tau d
+                TRY(cg_fp32(u, rg, x, sigma, stop, max_inner, s_is_neg_rg, sig_est));
+            } else {
+                TRY(lin(x, 0.0, rg, 0.0, nullptr));
+                TRY(lin(r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
+                TRY(lin(p, 1.0, r, 0.0, nullptr));
+                PULL(ds);
+                rr = sc(SL_RRA);
+            }
+            if (!in && rr > 0.0) {
                 // device-driven chunks (k_cg_ctl); the host reads the block once per chunk
                 double* hsc = h->h_scal;
                 hsc[SL_SIG] = sigma; hsc[SL_STOP] = stop; hsc[SL_MAXIN] = (double)max_inner;
@@ -362,7 +477,7 @@ struct Solver {
             // ---- direction xi = s + tau d (Eq. xi), kept in x ----
             if (s_is_neg_rg) {
                 TRY(lin(x, -1.0, rg, 0.0, nullptr));
-            } else if (have_d) {
+            } else if (have_d && !in) {
                 TRY(Ops<T>::dot2(g, w, p, rg, p, Hp, SL_D0, s));
                 PULL(ds);
                 const double tau = sc(SL_D0) / sc(SL_D0 + 1);
@@ -831,9 +946,13 @@ struct BatchSolver {
 #undef TRY
 };
 
+int solve_one(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+              sbec_stats* stats, const InnerCg* inner);
+
 bool opts_valid(const sbec_solve_opts& o) {
     return o.retraction >= 1 && o.retraction <= 3 && o.tol > 0.0 && o.maxit >= 0 && o.rgbb_maxit >= 0 &&
-           o.cg_chunk >= 1 && o.cg_chunk <= 64 && (o.cuda_graphs == 0 || o.cuda_graphs == 1);
+           o.cg_chunk >= 1 && o.cg_chunk <= 64 && (o.cuda_graphs == 0 || o.cuda_graphs == 1) &&
+           (o.refine_cg_fp32 == 0 || o.refine_cg_fp32 == 1);
 }
 
 }  // namespace
@@ -851,6 +970,7 @@ void sbec_solve_defaults(sbec_solve_opts* o) {
     o->project_initial = 1;
     o->cg_chunk = 4;
     o->cuda_graphs = 1;
+    o->refine_cg_fp32 = 1;
 }
 
 int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
@@ -883,6 +1003,16 @@ int sbec_solve_workspace_bytes(const sbec_handle* h, size_t* bytes) {
 
 int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
                sbec_stats* stats) {
+    return solve_one(h, X, opts, workspace, workspace_bytes, stats, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+// sbec_solve, optionally with the modified CG of an FP64 solve on an FP32 context
+int solve_one(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
+              sbec_stats* stats, const InnerCg* inner) {
     if (!h || !X || !workspace) return SBEC_ERR_ARG;
     if (workspace_bytes < 10 * h->field_bytes || !sbec_is_device_ptr(workspace)) return SBEC_ERR_ARG;
     if (h->B != 1) return SBEC_ERR_ARG;       // batches: sbec_solve_batch
@@ -902,13 +1032,14 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
     }
     int rc;
     if (h->prob.precision == SBEC_FP64) {
-        Solver<double> S(h, o, workspace, st);
+        Solver<double> S(h, o, workspace, st, inner);
         rc = S.run(Xd);
     } else {
         Solver<float> S(h, o, workspace, st);
         rc = S.run(Xd);
     }
     if (clear_skip(h) && rc == SBEC_OK) rc = SBEC_ERR_CUDA;
+    if (inner && clear_skip(inner->h) && rc == SBEC_OK) rc = SBEC_ERR_CUDA;
     h->last_grad_X = nullptr;
     if (host && (rc == SBEC_OK || rc == SBEC_ERR_NOCONV)) {
         if (cudaMemcpyAsync(X, Xd, h->field_bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
@@ -918,16 +1049,8 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
     return rc;
 }
 
-}  // extern "C"
-
-namespace {
-template <typename TS, typename TD>
-__global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = TD(src[i]);
-}
-
 }  // namespace
+
 
 extern "C" {
 
@@ -975,6 +1098,13 @@ int sbec_solve_mixed(sbec_handle* h64, sbec_handle* h32, void* X, const sbec_sol
     if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
     sbec_solve_opts of = o;
     of.project_initial = 1;            // the float state is back on M to double precision
+    if (h64->B == 1 && o.refine_cg_fp32) {
+        // the FP32 phase is over: its fields hold the inner CG's float vectors
+        InnerCg in;
+        in.h = h32;
+        for (int i = 0; i < 6; ++i) in.f[i] = static_cast<char*>(ws32) + (size_t)i * h32->field_bytes;
+        return solve_one(h64, X, &of, ws64, 10 * h64->field_bytes, st_fp64, &in);
+    }
     return phase(h64, X, &of, ws64, st_fp64);
 }
 
@@ -1023,6 +1153,34 @@ int sbec_solve_cascadic(sbec_handle* const* levels, int nlevels, void* const* X,
         oj.project_initial = (j == 0) ? o.project_initial : 0;     // the prolongation ends with R1
         sbec_stats local;
         rc = sbec_solve(levels[j], X[j], &oj, workspace, workspace_bytes, finest && stats ? stats : &local);
+        if (rc != SBEC_OK && !(rc == SBEC_ERR_NOCONV && !finest)) return rc;
+    }
+    return rc;
+}
+
+// Cascadic multigrid with the mixed form on every level: sbec_solve_mixed per
+// level (FP32 phase, FP64 refinement), prolongation of the refined FP64 state.
+int sbec_solve_cascadic_mixed(sbec_handle* const* levels64, sbec_handle* const* levels32, int nlevels,
+                              void* const* X, const sbec_solve_opts* opts, double tol_coarse, double tol_mixed,
+                              void* workspace, size_t workspace_bytes, sbec_stats* st_mixed, sbec_stats* st_fp64) {
+    if (!levels64 || !levels32 || !X || nlevels < 1) return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    int rc = SBEC_OK;
+    for (int j = 0; j < nlevels; ++j) {
+        if (!levels64[j] || !levels32[j] || !X[j]) return SBEC_ERR_ARG;
+        if (levels64[j]->B != 1) return SBEC_ERR_ARG;
+        if (j > 0) {
+            rc = sbec_prolongate(levels64[j - 1], X[j - 1], levels64[j], X[j]);
+            if (rc) return rc;
+        }
+        sbec_solve_opts oj = o;
+        const bool finest = (j == nlevels - 1);
+        oj.tol = finest ? o.tol : (tol_coarse > o.tol ? tol_coarse : o.tol);
+        oj.project_initial = (j == 0) ? o.project_initial : 0;
+        sbec_stats lm, lf;
+        rc = sbec_solve_mixed(levels64[j], levels32[j], X[j], &oj, tol_mixed, workspace, workspace_bytes,
+                              finest && st_mixed ? st_mixed : &lm, finest && st_fp64 ? st_fp64 : &lf);
         if (rc != SBEC_OK && !(rc == SBEC_ERR_NOCONV && !finest)) return rc;
     }
     return rc;

@@ -65,7 +65,7 @@ for _f in ("sbec_create", "sbec_destroy", "sbec_energy", "sbec_grad", "sbec_hess
 
 EXPORTED = ("sbec_create", "sbec_destroy", "sbec_energy", "sbec_grad", "sbec_hessvec",
             "sbec_retract", "sbec_sync", "sbec_scalars", "sbec_status_string",
-            "sbec_launch_count", "sbec_profile", "sbec_profile_read")
+            "sbec_launch_count", "sbec_profile", "sbec_profile_read", "sbec_probe_fma_peak")
 
 
 class SbecError(RuntimeError):
@@ -306,14 +306,26 @@ def library_symbols():
     return [name for name in EXPORTED if hasattr(_lib, name)]
 
 
+_lib.sbec_probe_fma_peak.argtypes = [_int, _int, _dp]
+_lib.sbec_probe_fma_peak.restype = _int
+
+
+def probe_fma_peak(precision="fp64", iters=None):
+    """Measured FMA rate of the current device in GFLOP/s (sbec_probe_fma_peak):
+    the FP64 rate bounds the FP64 form of the hot path."""
+    fp64 = precision == "fp64"
+    if iters is None:
+        iters = 20000 if fp64 else 400000
+    g = ctypes.c_double()
+    _check(_lib.sbec_probe_fma_peak(FP64 if fp64 else MIXED, int(iters), ctypes.byref(g)), "sbec_probe_fma_peak")
+    return g.value
+
+
 _lib.sbec_energy_noalloc.argtypes = [ctypes.POINTER(Problem), _vp, _vp, _dp, _vp]
 _lib.sbec_energy_noalloc.restype = _int
 
 
-def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
-    """E_h(X) through sbec_energy_noalloc: no handle and no device allocation, for
-    callers that cannot allocate device memory where they need the energy.  X and
-    V (None: harmonic trap) must be device tensors; FP64 only."""
+def _noalloc_problem(F, n, lo, hi, beta, M, p, q):
     n = tuple(int(v) for v in n)
     dim = len(n)
     pr = Problem()
@@ -326,8 +338,25 @@ def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
     for i in range(4):
         pr.beta[i] = float(b[i])
     pr.p, pr.q, pr.M, pr.precision = float(p), float(q), float(M), FP64
+    return pr
+
+
+def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
+    """E_h(X) through sbec_energy_noalloc: no handle and no device allocation, for
+    callers that cannot allocate device memory where they need the energy.  X and
+    V (None: harmonic trap) must be contiguous device tensors (complex128 state,
+    float64 potential); FP64 only."""
+    import torch
+    C, G = 2 * int(F) + 1, int(np.prod([int(v) for v in n]))
+    # the kernels read X and V in place through raw pointers: check what they will read
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.complex128
+            and X.is_contiguous() and X.numel() == C * G):
+        raise ValueError(f"X must be a contiguous complex128 CUDA tensor of {C} x {G} values")
+    if V is not None and not (isinstance(V, torch.Tensor) and V.is_cuda and V.dtype == torch.float64
+                              and V.is_contiguous() and V.numel() == G and V.device == X.device):
+        raise ValueError(f"V must be a contiguous float64 CUDA tensor of {G} values on X's device")
+    pr = _noalloc_problem(F, n, lo, hi, beta, M, p, q)
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream().cuda_stream
     E = ctypes.c_double()
     _check(_lib.sbec_energy_noalloc(ctypes.byref(pr), _ptr(V), _ptr(X), ctypes.byref(E), stream),
@@ -335,10 +364,24 @@ def energy_noalloc(F, n, lo, hi, beta, M, X, p=0.0, q=0.0, V=None, stream=None):
     return E.value
 
 
+def energy_noalloc_raw(F, n, lo, hi, beta, M, X_ptr, p=0.0, q=0.0, V_ptr=0, stream=None):
+    """sbec_energy_noalloc on raw addresses, without the checks of energy_noalloc;
+    returns the status code (the energy is discarded).  For testing the entry
+    point's own argument checks."""
+    pr = _noalloc_problem(F, n, lo, hi, beta, M, p, q)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    E = ctypes.c_double()
+    return int(_lib.sbec_energy_noalloc(ctypes.byref(pr), ctypes.c_void_p(V_ptr or None),
+                                        ctypes.c_void_p(X_ptr), ctypes.byref(E), stream))
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("retraction", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("rgbb_tol", ctypes.c_double), ("rgbb_maxit", ctypes.c_int),
-                ("project_initial", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("cuda_graphs", ctypes.c_int)]
+                ("project_initial", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("cuda_graphs", ctypes.c_int),
+                ("refine_cg_fp32", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -358,7 +401,8 @@ _lib.sbec_solve.restype = _int
 ARNT, RGBB = 0, 1
 
 
-def _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project=True, cg_chunk=None, graphs=None):
+def _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project=True, cg_chunk=None, graphs=None,
+          refine_cg_fp32=None):
     """sbec_solve_opts from the library defaults and the given overrides (None keeps the
     default: 4 CG iterations per chunk, CUDA graphs on)."""
     o = SolveOpts()
@@ -370,6 +414,8 @@ def _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project=True, cg
         o.cg_chunk = int(cg_chunk)
     if graphs is not None:
         o.cuda_graphs = int(bool(graphs))
+    if refine_cg_fp32 is not None:
+        o.refine_cg_fp32 = int(bool(refine_cg_fp32))
     return o
 
 
@@ -403,11 +449,12 @@ _lib.sbec_solve_mixed.restype = _int
 
 
 def solve_mixed(h64, h32, X, tol=1e-8, tol_mixed=1e-3, method="arnt", retraction=1, maxit=10000,
-                rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None, graphs=None):
+                rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None, graphs=None, refine_cg_fp32=None):
     """Mixed-precision solve on h32 then FP64 refinement on h64 (sbec_solve_mixed).
-    X: complex128 device tensor, overwritten.  Returns (stats_mixed, stats_fp64), dicts
+    X: complex128 device tensor, overwritten.  refine_cg_fp32 (default on): the
+    refinement's modified CG runs on h32.  Returns (stats_mixed, stats_fp64), dicts
     for single handles and lists of B dicts for batch handles."""
-    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs)
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs, refine_cg_fp32)
     nb = ctypes.c_size_t()
     _check(_lib.sbec_solve_mixed_workspace_bytes(h64._h, h32._h, ctypes.byref(nb)),
            "sbec_solve_mixed_workspace_bytes")
@@ -457,6 +504,39 @@ def solve_cascadic(handles, states, tol=1e-8, tol_coarse=1e-5, method="arnt", re
     out = {k: getattr(st, k) for k, _ in Stats._fields_}
     out["status"] = rc
     return out
+
+
+_lib.sbec_solve_cascadic_mixed.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp),
+                                           ctypes.POINTER(SolveOpts), _dbl, _dbl, _vp, ctypes.c_size_t,
+                                           ctypes.POINTER(Stats), ctypes.POINTER(Stats)]
+_lib.sbec_solve_cascadic_mixed.restype = _int
+
+
+def solve_cascadic_mixed(handles64, handles32, states, tol=1e-8, tol_coarse=1e-5, tol_mixed=1e-3, method="arnt",
+                         retraction=1, maxit=10000, rgbb_tol=1e-2, rgbb_maxit=2000, workspace=None, cg_chunk=None,
+                         graphs=None, refine_cg_fp32=None):
+    """sbec_solve_cascadic_mixed: per level a mixed solve with FP64 refinement, coarse to
+    fine; states[j] (complex128 device tensors) is level j's array.  Returns the
+    (mixed, fp64) stats dicts of the finest level."""
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, True, cg_chunk, graphs, refine_cg_fp32)
+    nb = ctypes.c_size_t()
+    _check(_lib.sbec_solve_mixed_workspace_bytes(handles64[-1]._h, handles32[-1]._h, ctypes.byref(nb)),
+           "sbec_solve_mixed_workspace_bytes")
+    if workspace is None:
+        import torch
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    h64 = (_vp * len(handles64))(*[h._h for h in handles64])
+    h32 = (_vp * len(handles32))(*[h._h for h in handles32])
+    xs = (_vp * len(states))(*[_ptr(x) for x in states])
+    sm, sf = Stats(), Stats()
+    rc = _lib.sbec_solve_cascadic_mixed(h64, h32, len(handles64), xs, ctypes.byref(o), float(tol_coarse),
+                                        float(tol_mixed), _ptr(workspace), nb.value, ctypes.byref(sm),
+                                        ctypes.byref(sf))
+    if rc not in (OK, ERR_NOCONV):
+        _check(rc, "sbec_solve_cascadic_mixed")
+    a = {k: getattr(sm, k) for k, _ in Stats._fields_}
+    b = dict({k: getattr(sf, k) for k, _ in Stats._fields_}, status=rc)
+    return a, b
 
 
 _lib.sbec_solve_batch.argtypes = [_vp, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.c_size_t, ctypes.POINTER(Stats)]

@@ -155,10 +155,11 @@ def spin3_3d_cascadic() -> Workload:
 
 def spin3_3d_256() -> Workload:
     """Spin-3, 3D, 256^3 on [-10,10]^3, V = harmonic + 10 sum sin^2(pi x_i / 2),
-    beta = (1000, -5, 10, 2), M = 0."""
+    beta = (1000, -5, 10, 2), M = 0.  Its ground state is computed cascadically from the
+    coarse levels n/4 and n/2 (64^3, 128^3)."""
     return Workload("spin3_3d_256cubed", F=3, n=(256, 256, 256), lo=(-10.0,) * 3, hi=(10.0,) * 3,
                     beta=(1000.0, -5.0, 10.0, 2.0), M=0.0, lattice_amp=10.0,
-                    lattice_k=np.pi / 2, seed=SEED_BASE + 5)
+                    lattice_k=np.pi / 2, seed=SEED_BASE + 5, levels=((64, 64, 64), (128, 128, 128)))
 
 
 def paper_spin2_2d(M: float, n: int = 256) -> Workload:

@@ -63,4 +63,22 @@ def test_roofline_picks_the_longest_modelled_kernel():
     assert r["kernel"] == "x_inv_hess" and r["bound"] == "alu"
     fl = math.prod(w.n) * bench.PW_FLOPS["hess"][w.F]
     assert r["achieved"] == pytest.approx(fl / 4.0e-3 / 1e9)
-    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_GFLOPS)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_NOMINAL_GFLOPS)
+    # with a measured FP64 rate the fraction is of that rate
+    r = bench.roofline_of(prof, w, "fp64", 1, w.name, fp64_peak=1000.0)
+    assert r["peak"] == 1000.0 and r["frac"] == pytest.approx(r["achieved"] / 1000.0)
+    assert r["peak_source"].startswith("measured")
+
+
+def test_cpu_sample_slab_of_large_grids():
+    # grids above 2^21 points are sampled on a z-slab of 2^20 points of the same
+    # workload (same spacing and potential values), scaled by the slab's share
+    import numpy as np
+    from paper_1907_01194_gb300 import workloads as W
+    w = bench.workload("spin3_3d_256")
+    ws, share, desc = bench.cpu_workload_sample(w)
+    assert ws.n == (256, 256, 16) and share == pytest.approx(1 / 16)
+    assert ws.dV == pytest.approx(w.dV, rel=1e-15)
+    assert np.array_equal(W.potential(ws), W.potential(w)[120:136])
+    small = bench.workload("spin2_2d")
+    assert bench.cpu_workload_sample(small)[0] is small

@@ -51,7 +51,7 @@ def test_solve_defaults_and_option_layout(lib):
     sbec._lib.sbec_solve_defaults(ctypes.byref(o))
     assert (o.method, o.retraction, o.tol, o.maxit) == (sbec.ARNT, 1, 1e-6, 10000)
     assert (o.rgbb_tol, o.rgbb_maxit, o.project_initial) == (1e-2, 2000, 1)
-    assert (o.cg_chunk, o.cuda_graphs) == (4, 1)
+    assert (o.cg_chunk, o.cuda_graphs, o.refine_cg_fp32) == (4, 1, 1)
     hdr = open(os.path.join(ROOT, "include", "sbec.h")).read()
     body = hdr[hdr.index("typedef struct sbec_solve_opts"):hdr.index("} sbec_solve_opts;")]
     fields = re.findall(r"^\s*(?:int|double)\s+(\w+);", body, re.M)

@@ -66,3 +66,28 @@ def test_cascadic_solve_matches_oracle(w, levels, dev):
             h.close()
     assert st["converged"] and ost.converged
     assert abs(st["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+
+
+def test_cascadic_mixed_solve_matches_oracle(dev):
+    # sbec_solve_cascadic_mixed: every level a mixed solve with FP64 refinement (FP32
+    # Newton CG); the finest energy meets the oracle's FP64 cascadic solve to 1e-10
+    from paper_1907_01194_gb300 import sbec
+    w = W.Workload("casc3d", F=3, n=(16, 16, 16), lo=(-8.0,) * 3, hi=(8.0,) * 3, beta=(500.0, -2.0, 5.0, -1.0),
+                   M=0.2)
+    ws = [w.at((8, 8, 8)), w]
+    P = [_P(x) for x in ws]
+    X0 = W.initial_fields(ws[0])
+    Xs, ost, _ = O.solve(P, O.to_matrix(P[0], X0), O.SolveOptions(tol=1e-9))
+    h64 = [sbec.Handle.from_workload(x) for x in ws]
+    h32 = [sbec.Handle.from_workload(x, precision="mixed") for x in ws]
+    states = [torch.from_numpy(X0).to(dev)] + [torch.empty((x.C,) + x.shape, dtype=torch.complex128, device=dev)
+                                                 for x in ws[1:]]
+    try:
+        sm, sf = sbec.solve_cascadic_mixed(h64, h32, states, tol=1e-9)
+        E, gn = h64[-1].grad(states[-1])
+    finally:
+        for h in h64 + h32:
+            h.close()
+    assert sf["converged"] and ost.converged and gn <= 1e-9
+    assert abs(sf["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+    assert abs(E - ost.energy) <= 1e-10 * abs(ost.energy)

@@ -135,16 +135,22 @@ def test_host_array_solve_matches_device(dev):
     assert np.array_equal(Xd.cpu().numpy(), Xh)
 
 
-def test_mixed_solve_with_fp64_refinement(dev):
-    # a13: FP32 FFT / pointwise solve, then FP64 refinement; the refined energy meets
-    # the FP64 oracle's to 1e-10 relative (the bar for the mixed form is 1e-7)
+@pytest.mark.parametrize("cg32", [True, False], ids=["refine_cg_fp32", "refine_cg_fp64"])
+def test_mixed_solve_with_fp64_refinement(cg32, dev):
+    # a13: FP32 FFT / pointwise solve, then FP64 refinement (its Newton systems solved
+    # in FP32 or FP64); the refined energy meets the FP64 oracle's to 1e-10 relative
+    # (the bar for the mixed form is 1e-7) and the FP64 gradient norm the tolerance
     from paper_1907_01194_gb300 import sbec
     w = CASES[1][0]
     X0 = W.initial_fields(w)
     X = torch.from_numpy(X0).to(dev)
     with sbec.Handle.from_workload(w) as h64, sbec.Handle.from_workload(w, precision="mixed") as h32:
-        sm, sf = sbec.solve_mixed(h64, h32, X, tol=1e-9, tol_mixed=1e-3)
+        sm, sf = sbec.solve_mixed(h64, h32, X, tol=1e-9, tol_mixed=1e-3, refine_cg_fp32=cg32)
+        E, gn = h64.grad(X)
     P, ost = _oracle_solve(w, X0, 1e-9)
-    assert sf["converged"]
+    assert sf["converged"] and gn <= 1e-9
     assert sm["n_hvp"] + sm["n_grad"] > 0
     assert abs(sf["energy"] - ost.energy) <= 1e-10 * abs(ost.energy)
+    assert abs(E - ost.energy) <= 1e-10 * abs(ost.energy)
+    N, Mg = _constraints(w, X.cpu().numpy())
+    assert abs(N - 1) < 1e-12 and abs(Mg - w.M) < 1e-12
