@@ -87,6 +87,8 @@ def parse():
                     choices=["spin1_1d", "spin2_2d", "spin3_3d_128", "spin3_3d_256", "batch512"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paper-table", action="store_true",
+                    help="only the paper's ARNT/RGBB x R1/R2/R3 comparison on its spin-2 2D case")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-ground-state solves")
     ap.add_argument("--solve-maxit", type=int, default=10000,
                     help="outer-iteration cap of each level of the time-to-ground-state solves")
@@ -756,11 +758,57 @@ def paper_case(args, sbec, torch, dev, stream):
             "runs": runs}
 
 
+# The paper's algorithm comparison (Sec. 7.1, tables of ARNT / RGBB with the retractions
+# R1 / R2 / R3, the comparison system RTR left out): its spin-2 2D case, columns f, nrmG,
+# iter, time; for ARNT "iter" is outer iterations (average inner CG iterations) on the
+# finest mesh, for RGBB the RGBB iterations there.
+PAPER_TABLE_M = (0.0, 0.5, 1.5)
+
+
+def paper_table(args):
+    """ARNT and RGBB with R1, R2, R3 on the paper's spin-2 2D case (cascadic 64^2 ->
+    128^2 -> 256^2, tolerances 1e-5 / 1e-6, the paper's nematic initial spinor), timed
+    on this GPU; one JSON line with every row."""
+    import torch
+    from paper_1907_01194_gb300 import sbec
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for M in PAPER_TABLE_M:
+        ws = [W.paper_spin2_2d(M, n) for n in (64, 128, 256)]
+        hs = [sbec.Handle.from_workload(w, stream=stream.cuda_stream) for w in ws]
+        for h, w in zip(hs, ws):
+            h.autotune(torch.from_numpy(W.paper_initial(w)).to(dev))
+        for method in ("arnt", "rgbb"):
+            for retr in (1, 2, 3):
+                states = [torch.from_numpy(W.paper_initial(ws[0])).to(dev)] + [
+                    torch.empty((w.C,) + w.shape, dtype=torch.complex128, device=dev) for w in ws[1:]]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = sbec.solve_cascadic(hs, states, tol=1e-6, tol_coarse=1e-5, method=method, retraction=retr)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if method == "arnt":
+                    it = f"{st['outer_iters']} ({st['inner_iters'] / max(1, st['outer_iters']):.0f})"
+                else:
+                    it = f"{st['rgbb_iters']}"
+                rows.append({"M": M, "method": method.upper(), "retr": f"R{retr}", "f": st["energy"],
+                             "nrmG": st["grad_norm"], "iter": it, "seconds": dt, "converged": bool(st["converged"])})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        for h in hs:
+            h.close()
+    print(json.dumps({"paper_table": "spin-2 2D 256^2 x 5, beta = (243, 12.1, -13), [-8,8]^2 (Sec. 7.1)",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.paper_table:
+        return paper_table(args)
     return run_ours(args, world, rank, local)
 
 

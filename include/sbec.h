@@ -42,7 +42,7 @@ extern "C" {
 #endif
 
 #define SBEC_OK             0
-#define SBEC_ERR_ARG        1  /* bad argument: |M| >= F, F not in {1,2,3}, bad n, NULL */
+#define SBEC_ERR_ARG        1  /* bad argument: |M| >= F, F not in {1,..,4}, bad n, NULL */
 #define SBEC_ERR_DOMAIN     2  /* point outside the retraction's domain (Omega or S),
                                   u^T Gamma^2 u - M^2 <= 0, or root bracket failure */
 #define SBEC_ERR_NONFINITE  3  /* NaN or Inf in a reduction */
@@ -55,11 +55,14 @@ extern "C" {
                                   retraction scalars in double (state is float2) */
 
 /* Problem statement (Sec. 2-3).  beta[0..3] = (beta0, beta1, beta2, beta3):
- * density, spin, singlet (F >= 2) and quintet (F = 3) interaction strengths;
+ * density, spin, singlet (F >= 2) and quintet (F = 3) interaction strengths.
+ * F = 4: the paper prints the energy for F <= 3 only; a spin-4 condensate is
+ * modelled here with the density, spin and singlet-pair terms of the spin-2
+ * form (angular-momentum matrices and singlet pair of spin 4; beta3 unused);
  * p, q: linear and quadratic Zeeman shifts (b_l = -p l + q l^2); M: the
  * magnetisation; lo/hi: the box per axis (x, y, z). */
 typedef struct sbec_problem {
-    int    F;            /* spin: 1, 2 or 3 (C = 2F+1 components) */
+    int    F;            /* spin: 1, 2, 3 or 4 (C = 2F+1 components) */
     int    dim;          /* 1, 2 or 3 */
     int    n[3];         /* grid points per axis (x, y, z); unused axes: 1 */
     double lo[3], hi[3]; /* box per axis */

@@ -88,12 +88,39 @@ def spin_matrices(F: int):
                             [0, 0, 0, 0, 0, a, 0]], dtype=complex)
         fz = np.diag([3.0, 2.0, 1.0, 0.0, -1.0, -2.0, -3.0]).astype(complex)
     else:
-        raise ValueError("spin matrices are printed for F = 1, 2, 3 only")
+        return spin_matrices_general(F)
+    return fx, fy, fz
+
+
+def spin_matrices_general(F: int):
+    """(f_x, f_y, f_z) for any integer spin F: the angular-momentum matrices the
+    printed F = 1, 2, 3 ones are instances of (Sec. 2), in the basis l = F..-F.
+    f_z = diag(l); the raising matrix has (f_+)_{l+1, l} = sqrt(F(F+1) - l(l+1));
+    f_x = (f_+ + f_-)/2 and f_y = (f_+ - f_-)/(2i) with f_- = f_+^T.  The paper
+    prints the matrices for F <= 3 only; for F >= 4 this is the reading of its
+    claim that the method applies to any integer spin."""
+    C = 2 * F + 1
+    ls = np.arange(F, -F - 1, -1)
+    fp = np.zeros((C, C))
+    for j in range(1, C):                     # row j-1 holds l + 1, column j holds l
+        l = ls[j]
+        fp[j - 1, j] = math.sqrt(F * (F + 1) - l * (l + 1))
+    fm = fp.T
+    fx = (fp + fm).astype(complex) / 2.0
+    fy = (fp - fm).astype(complex) / 2.0j
+    fz = np.diag(ls.astype(float)).astype(complex)
     return fx, fy, fz
 
 
 def singlet_matrix(F: int):
-    """The singlet-pair matrix bold-A of Sec. 2 (F = 2: 1/sqrt5, F = 3: 1/sqrt7)."""
+    """The singlet-pair matrix bold-A of Sec. 2 (F = 2: 1/sqrt5, F = 3: 1/sqrt7).
+    For F >= 4 (reading): the same alternating anti-diagonal, A[j, 2F-j] =
+    (-1)^j / sqrt(2F+1), the pattern of the printed F = 2, 3 matrices."""
+    if F >= 4:
+        A = np.zeros((2 * F + 1, 2 * F + 1))
+        for j in range(2 * F + 1):
+            A[j, 2 * F - j] = (-1.0) ** j
+        return A / math.sqrt(2 * F + 1.0)
     if F == 2:
         A = np.zeros((5, 5))
         for j, s in enumerate([1, -1, 1, -1, 1]):
@@ -177,7 +204,7 @@ class Problem:
         self.lo = tuple(float(v) for v in self.lo)
         self.hi = tuple(float(v) for v in self.hi)
         self.d = len(self.n)
-        assert self.F in (1, 2, 3)
+        assert isinstance(self.F, int) and self.F >= 1
         assert len(self.lo) == self.d and len(self.hi) == self.d
         self.C = 2 * self.F + 1
         self.shape = tuple(reversed(self.n))          # (n_z, n_y, n_x)

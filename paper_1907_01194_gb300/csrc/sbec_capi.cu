@@ -168,7 +168,7 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     if (!probs || !out || B < 1) return SBEC_ERR_ARG;
     *out = nullptr;
     const sbec_problem& P = probs[0];
-    if (P.F < 1 || P.F > 3 || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
+    if (P.F < 1 || P.F > sbec::kMaxF || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
     if (P.precision != SBEC_FP64 && P.precision != SBEC_MIXED) return SBEC_ERR_ARG;
     for (int ax = 0; ax < 3; ++ax) {
         if (ax < P.dim) {
@@ -211,7 +211,7 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     g.dV = dV;
     g.invG = 1.0 / (double)g.G;
     g.M = P.M;
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < sbec::kMaxC; ++i) {
         const double l = (double)(P.F - i);
         g.bz[i] = (i < g.C) ? (-P.p * l + P.q * l * l) : 0.0;
     }
@@ -219,7 +219,7 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     auto params = [&](const sbec_problem& Q, sbec::PointParams& pp) {
         const double b0 = Q.beta[0], b1 = Q.beta[1];
         const double b2 = Q.F >= 2 ? Q.beta[2] : 0.0, b3 = Q.F == 3 ? Q.beta[3] : 0.0;
-        for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
+        for (int i = 0; i < sbec::kMaxC; ++i) pp.bz[i] = g.bz[i];
         pp.g0 = 2 * b0 / dV; pp.g1 = 2 * b1 / dV; pp.g2 = 2 * b2 / dV; pp.g3 = 2 * b3 / dV;
         pp.e0 = b0 / (2 * dV); pp.e1 = b1 / (2 * dV); pp.e2 = b2 / (2 * dV); pp.e3 = b3 / (2 * dV);
     };

@@ -381,6 +381,7 @@ template <int C> struct InvSqrtC;
 template <> struct InvSqrtC<3> { static constexpr double v = 0.57735026918962576451; };
 template <> struct InvSqrtC<5> { static constexpr double v = 0.44721359549995793928; };
 template <> struct InvSqrtC<7> { static constexpr double v = 0.37796447300922722721; };
+template <> struct InvSqrtC<9> { static constexpr double v = 0.33333333333333333333; };
 
 template <> struct Spin<1> {
     static constexpr int C = 3;
@@ -398,6 +399,19 @@ template <> struct Spin<3> {
         return (i == 0 || i == 5) ? 2.4494897427831780982            // sqrt6
              : (i == 1 || i == 4) ? 3.1622776601683793320            // sqrt10
                                   : 3.4641016151377545871;           // sqrt12
+    }
+};
+
+// F = 4 (and any higher F): the same ladder constants sqrt(F(F+1) - (l-1) l),
+// l = F - i; the paper prints the spin matrices up to F = 3 only, and a spin-4
+// condensate is modelled with the density, spin and singlet-pair terms
+template <> struct Spin<4> {
+    static constexpr int C = 9;
+    __device__ static constexpr double lad(int i) {
+        return (i == 0 || i == 7) ? 2.8284271247461900976            // sqrt8
+             : (i == 1 || i == 6) ? 3.7416573867739413856            // sqrt14
+             : (i == 2 || i == 5) ? 4.2426406871192851464            // sqrt18
+                                  : 4.4721359549995793928;           // sqrt20
     }
 };
 
@@ -431,10 +445,10 @@ __device__ __forceinline__ constexpr int qnt_l(int k) { return 2 - k; }
 // PointParams in the arithmetic type of the pointwise code (converted once per
 // thread, so that the FP32 kernels do no FP64 arithmetic per point).
 template <typename T> struct PPT {
-    T bz[7], g0, g1, g2, g3, e0, e1, e2, e3;
+    T bz[kMaxC], g0, g1, g2, g3, e0, e1, e2, e3;
     __device__ __forceinline__ explicit PPT(const PointParams& p) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i) bz[i] = T(p.bz[i]);
+        for (int i = 0; i < kMaxC; ++i) bz[i] = T(p.bz[i]);
         g0 = T(p.g0); g1 = T(p.g1); g2 = T(p.g2); g3 = T(p.g3);
         e0 = T(p.e0); e1 = T(p.e1); e2 = T(p.e2); e3 = T(p.e3);
     }
@@ -470,6 +484,8 @@ struct Dens {
             caxpy(A00, T((F & 1) ? -1.0 : 1.0) * sg, cmul(x[F], x[F]));
         }
         if (F == 3) {
+            // A_{2l} is a symmetric bilinear form: each unordered pair (i, ip) once,
+            // off-diagonal pairs with twice the entry
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const int l = qnt_l(k);
@@ -477,7 +493,8 @@ struct Dens {
 #pragma unroll
                 for (int i = 0; i < C; ++i) {
                     const int ip = 2 * F - l - i;
-                    if (ip >= 0 && ip < C && qnt_entry(k, i) != 0.0) caxpy(s, T(qnt_entry(k, i)), cmul(x[i], x[ip]));
+                    if (ip >= i && ip < C && qnt_entry(k, i) != 0.0)
+                        caxpy(s, T((ip > i ? 2.0 : 1.0) * qnt_entry(k, i)), cmul(x[i], x[ip]));
                 }
                 A2[k] = s;
             }
@@ -503,25 +520,35 @@ struct Dens {
 };
 
 // Gradient (Eq. 3.12) at one grid point, component k, given the Laplacian term lx_k.
+// The interaction prefactors are applied to the densities once per point (g1/2 F_-,
+// g2 A00 / sqrt(2F+1), g3 A_{2l}), so that each component's terms are plain complex
+// products with the compile-time ladder / pair constants.
 template <int F, typename T2>
 __device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<F, T2>& D, decltype(T2::x) V,
                                            const PPT<decltype(T2::x)>& pp, const T2 (&lx)[2 * F + 1],
                                            T2 (&g)[2 * F + 1]) {
     using T = decltype(T2::x);
     constexpr int C = 2 * F + 1;
-    const T g0 = T(pp.g0), g1 = T(pp.g1), g2 = T(pp.g2), g3 = T(pp.g3);
-    const T2 Fm = cconj(D.Fp);
+    const T gr = T(2) * V + pp.g0 * D.rho;          // 2 V + g0 rho
+    const T gFz = pp.g1 * D.Fz;
+    const T2 hFm = cscale(cconj(D.Fp), T(0.5) * pp.g1);
+    T2 gA00 = mk<T2>(0, 0);
+    if (F >= 2) gA00 = cscale(D.A00, pp.g2 * T(InvSqrtC<C>::v));
+    T2 gA2[5];
+    if (F == 3) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) gA2[q] = cscale(D.A2[q], pp.g3);
+    }
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         T2 r = lx[k];
-        const T lin = T(2) * (V + T(pp.bz[k])) + g0 * D.rho + g1 * T(F - k) * D.Fz;
-        caxpy(r, lin, x[k]);
+        caxpy(r, gr + T(2) * pp.bz[k] + T(F - k) * gFz, x[k]);
         // (g1/2) (F_- (f_+ x)_k + F_+ (f_- x)_k)
-        if (k + 1 < C) cfma(r, cscale(Fm, T(0.5) * g1 * T(Spin<F>::lad(k))), x[k + 1]);
-        if (k >= 1) cfma(r, cscale(D.Fp, T(0.5) * g1 * T(Spin<F>::lad(k - 1))), x[k - 1]);
+        if (k + 1 < C) cfma(r, cscale(hFm, T(Spin<F>::lad(k))), x[k + 1]);
+        if (k >= 1) cfma(r, cscale(cconj(hFm), T(Spin<F>::lad(k - 1))), x[k - 1]);
         if (F >= 2) {
-            const T sg = T((k & 1) ? -1.0 : 1.0) * T(InvSqrtC<C>::v);
-            cfma(r, cscale(D.A00, g2 * sg), cconj(x[C - 1 - k]));
+            const T2 t = cmul(gA00, cconj(x[C - 1 - k]));
+            if (k & 1) r = csub(r, t); else r = cadd(r, t);
         }
         if (F == 3) {
 #pragma unroll
@@ -529,14 +556,17 @@ __device__ __forceinline__ void grad_point(const T2 (&x)[2 * F + 1], const Dens<
                 const int l = qnt_l(q);
                 const int kp = 2 * F - l - k;
                 if (kp >= 0 && kp < C && qnt_entry(q, k) != 0.0)
-                    cfma(r, cscale(D.A2[q], g3 * T(qnt_entry(q, k))), cconj(x[kp]));
+                    cfma(r, cscale(gA2[q], T(qnt_entry(q, k))), cconj(x[kp]));
             }
         }
         g[k] = r;
     }
 }
 
-// Hessian-vector product (Eq. 3.13) at one grid point, given lz_k = (L Z)_k.
+// Hessian-vector product (Eq. 3.13) at one grid point, given lz_k = (L Z)_k.  As in
+// grad_point the prefactors are applied to the densities and to their directional
+// derivatives once per point; each coupling of component k is then
+// c (D z_j + dD x_j) with one complex product, one complex FMA and one scaling.
 template <int F, typename T2>
 __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&z)[2 * F + 1],
                                            const Dens<F, T2>& D, decltype(T2::x) V,
@@ -544,7 +574,6 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
                                            T2 (&hz)[2 * F + 1]) {
     using T = decltype(T2::x);
     constexpr int C = 2 * F + 1;
-    const T g0 = T(pp.g0), g1 = T(pp.g1), g2 = T(pp.g2), g3 = T(pp.g3);
     // directional derivatives of the densities
     T drho = 0, dFz = 0;
 #pragma unroll
@@ -553,18 +582,18 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
         drho += re;
         dFz += T(F - i) * re;
     }
-    drho *= T(2); dFz *= T(2);
     T2 dFp = mk<T2>(0, 0);
 #pragma unroll
     for (int i = 0; i < C - 1; ++i) {
         const T2 t = cadd(cmulc(z[i], x[i + 1]), cmulc(x[i], z[i + 1]));
         caxpy(dFp, T(Spin<F>::lad(i)), t);
     }
+    // dA00 = 2 z^T A x and dA_{2l} = 2 z^T A_l x (directional derivatives of x^T A x)
     T2 dA00 = mk<T2>(0, 0);
     if (F >= 2) {
-        const T sg = T(InvSqrtC<C>::v);
 #pragma unroll
-        for (int i = 0; i < C; ++i) caxpy(dA00, T((i & 1) ? -2.0 : 2.0) * sg, cmul(z[i], x[C - 1 - i]));
+        for (int i = 0; i < C; ++i)
+            caxpy(dA00, T(((i & 1) ? -2.0 : 2.0) * InvSqrtC<C>::v), cmul(z[i], x[C - 1 - i]));
     }
     T2 dA2[5];
     if (F == 3) {
@@ -580,27 +609,47 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
             dA2[q] = s;
         }
     }
-    const T2 Fm = cconj(D.Fp), dFm = cconj(dFp);
+    // prefactors applied once: (g1/2) F_-, (g1/2) dF_-, g2 A00 / sqrt(2F+1),
+    // g2 dA00 / sqrt(2F+1), g3 A_{2l}, g3 dA_{2l}; the scalar terms
+    // 2V + g0 rho + g1 m F_z and 2 g0 Re(x^* z) + 2 g1 m Re(x^* f_z z)
+    const T gr = T(2) * V + pp.g0 * D.rho;
+    const T gFz = pp.g1 * D.Fz;
+    const T gdr = T(2) * pp.g0 * drho, gdFz = T(2) * pp.g1 * dFz;
+    const T2 hFm = cscale(cconj(D.Fp), T(0.5) * pp.g1), hdFm = cscale(cconj(dFp), T(0.5) * pp.g1);
+    T2 gA00 = mk<T2>(0, 0), gdA00 = mk<T2>(0, 0);
+    if (F >= 2) {
+        const T sg = pp.g2 * T(InvSqrtC<C>::v);
+        gA00 = cscale(D.A00, sg);
+        gdA00 = cscale(dA00, sg);
+    }
+    T2 gA2[5];
+    if (F == 3) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            gA2[q] = cscale(D.A2[q], pp.g3);
+            dA2[q] = cscale(dA2[q], pp.g3);
+        }
+    }
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         T2 r = lz[k];
         const T m = T(F - k);
-        caxpy(r, T(2) * (V + T(pp.bz[k])) + g0 * D.rho + g1 * m * D.Fz, z[k]);
-        caxpy(r, g0 * drho + g1 * m * dFz, x[k]);
+        caxpy(r, gr + T(2) * pp.bz[k] + m * gFz, z[k]);
+        caxpy(r, gdr + m * gdFz, x[k]);
         if (k + 1 < C) {
-            const T c = T(0.5) * g1 * T(Spin<F>::lad(k));
-            cfma(r, cscale(Fm, c), z[k + 1]);
-            cfma(r, cscale(dFm, c), x[k + 1]);
+            T2 t = cmul(hFm, z[k + 1]);
+            cfma(t, hdFm, x[k + 1]);
+            caxpy(r, T(Spin<F>::lad(k)), t);
         }
         if (k >= 1) {
-            const T c = T(0.5) * g1 * T(Spin<F>::lad(k - 1));
-            cfma(r, cscale(D.Fp, c), z[k - 1]);
-            cfma(r, cscale(dFp, c), x[k - 1]);
+            T2 t = cmul(cconj(hFm), z[k - 1]);
+            cfma(t, cconj(hdFm), x[k - 1]);
+            caxpy(r, T(Spin<F>::lad(k - 1)), t);
         }
         if (F >= 2) {
-            const T sg = T((k & 1) ? -1.0 : 1.0) * T(InvSqrtC<C>::v) * g2;
-            cfma(r, cscale(D.A00, sg), cconj(z[C - 1 - k]));
-            cfma(r, cscale(dA00, sg), cconj(x[C - 1 - k]));
+            T2 t = cmul(gA00, cconj(z[C - 1 - k]));
+            cfma(t, gdA00, cconj(x[C - 1 - k]));
+            if (k & 1) r = csub(r, t); else r = cadd(r, t);
         }
         if (F == 3) {
 #pragma unroll
@@ -608,9 +657,9 @@ __device__ __forceinline__ void hess_point(const T2 (&x)[2 * F + 1], const T2 (&
                 const int l = qnt_l(q);
                 const int kp = 2 * F - l - k;
                 if (kp >= 0 && kp < C && qnt_entry(q, k) != 0.0) {
-                    const T c = g3 * T(qnt_entry(q, k));
-                    cfma(r, cscale(D.A2[q], c), cconj(z[kp]));
-                    cfma(r, cscale(dA2[q], c), cconj(x[kp]));
+                    T2 t = cmul(gA2[q], cconj(z[kp]));
+                    cfma(t, dA2[q], cconj(x[kp]));
+                    caxpy(r, T(qnt_entry(q, k)), t);
                 }
             }
         }

@@ -10,6 +10,10 @@
 
 namespace sbec {
 
+// Spins the kernels are instantiated for: F = 1..kMaxF (C = 2F + 1 components)
+constexpr int kMaxF = 4;
+constexpr int kMaxC = 2 * kMaxF + 1;
+
 // device scalar-block slots beyond the public SBEC_S_* ones
 enum {
     S_C2 = 7,          // u^T Gamma^2 u
@@ -19,14 +23,15 @@ enum {
     S_XFORM = 11,      // reserved
     S_SKIP = 12,       // nonzero: every kernel leaves this instance of a batch untouched
     S_TICKET = 13,     // blocks of the running launch that have stored their partials
-    S_SIG = 16,        // 7 retraction scales sigma_l (component index order)
+    S_SIG = 16,        // kMaxC retraction scales sigma_l (component index order)
     S_SOLVER = 32,     // solver scalars start here
     S_COUNT = 128
 };
+static_assert(S_SIG + kMaxC <= S_SOLVER, "retraction scales overlap the solver slots");
 
 // Physical parameters handed to the pointwise code (precomputed on the host).
 struct PointParams {
-    double bz[7];           // Zeeman diagonal b_l = -p l + q l^2 per component index
+    double bz[kMaxC];       // Zeeman diagonal b_l = -p l + q l^2 per component index
     double g0, g1, g2, g3;  // 2 beta_i / dV (gradient / Hessian prefactors)
     double e0, e1, e2, e3;  // beta_i / (2 dV) (energy prefactors)
 };
@@ -51,7 +56,7 @@ struct Geom {
     const double* lam2[3];    // lambda_p^2 per axis in DFT index order
     const void* k2s[3];       // lambda_p^2 / G per axis, T (precision of the handle)
     const void* V;            // potential, T
-    double bz[7];
+    double bz[kMaxC];
     double g0, g1, g2, g3, e0, e1, e2, e3;
     // batches: B instances of one shape stored [B][C][G] (V: [B][G]); per-instance
     // point parameters (beta) and magnetisations on the device, or null when B = 1

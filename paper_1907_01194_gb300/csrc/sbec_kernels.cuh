@@ -159,8 +159,8 @@ __device__ __forceinline__ void fin_proj_body(const double* pa, int na_tot, int 
                                               double M0, const double* Mb, double* scal0, int slot_a, int slot_b,
                                               int write_grad_info, int b, long long inst) {
     const int C = 2 * F + 1;
-    __shared__ double v[15];
-    int qs[15];
+    __shared__ double v[2 * kMaxC + 1];
+    int qs[2 * kMaxC + 1];
     int nq = 0;
     for (int i = 0; i < C; ++i) qs[nq++] = qn + i;
     for (int i = 0; i < C; ++i) qs[nq++] = qt + i;
@@ -762,11 +762,17 @@ __host__ __device__ constexpr size_t epi_stage_bytes() {
     return (size_t)(HESS ? 3 : 2) * (2 * F + 1) * kEpiThreads * sizeof(typename C2<T>::t) +
            (size_t)kEpiThreads * sizeof(T);
 }
+// Resident blocks per SM the epilogue is compiled for: two in FP32 (its pointwise
+// algebra fits 128 registers), one in FP64 (the FP64 pipe, not latency, bounds it)
+template <typename T> struct EpiBlocks { static constexpr int v = sizeof(T) == 4 ? 2 : 1; };
+
 // copies in flight: points k + 1 and k + 2 while point k is computed, when three
-// stages fit in 200 KB of shared memory, else point k + 1 only
+// stages of every resident block fit in 200 KB of shared memory, else point k + 1 only
 template <typename T, int F, bool HESS>
 __host__ __device__ constexpr int epi_stages() {
-    return 3 * epi_stage_bytes<T, F, HESS>() <= 200 * 1024 ? 3 : 2;
+    return 3 * EpiBlocks<T>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024   ? 3
+           : 2 * EpiBlocks<T>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024 ? 2
+                                                                              : 1;
 }
 template <typename T, int F, bool HESS>
 __host__ __device__ constexpr size_t epi_smem() {
@@ -774,7 +780,7 @@ __host__ __device__ constexpr size_t epi_smem() {
 }
 
 template <typename T, int F, bool HESS>
-__global__ void __launch_bounds__(kEpiThreads) k_epilogue(const XArgs a, const void* lxp, long long G) {
+__global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T>::v) k_epilogue(const XArgs a, const void* lxp, long long G) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
@@ -995,9 +1001,10 @@ constexpr double kEps = 2.220446049250313e-16;   // 2^-52
 
 __device__ __forceinline__ void retract_solve_body(const double* pa, int na_tot, int na_inst, int F, double M0,
                                                    const double* Mb, int kind, double* scal0, int b, long long inst) {
-    __shared__ double m[7];
+    __shared__ double m[kMaxC];
     const int C = 2 * F + 1;
-    const int qs[7] = {0, 1, 2, 3, 4, 5, 6};
+    int qs[kMaxC];
+    for (int i = 0; i < kMaxC; ++i) qs[i] = i;
     warp_sums(pa, na_tot, b * na_inst, na_inst, qs, C, m);
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
@@ -1105,7 +1112,7 @@ __device__ __forceinline__ void retract_solve_body(const double* pa, int na_tot,
     }
     const bool fin = !mine || isfinite(sig);
     ok = ok && (__all_sync(0xffffffffu, fin) != 0);
-    if (lane < 7) scal[S_SIG + lane] = mine ? sig : 0.0;
+    if (lane < kMaxC) scal[S_SIG + lane] = mine ? sig : 0.0;
     if (lane == 0 && !ok) set_status(scal, SBEC_ERR_DOMAIN);
 }
 
@@ -1493,7 +1500,7 @@ static int elem_grid(long long n, const Geom& g, const Work& w, int resident) {
 
 static PointParams point_params(const Geom& g) {
     PointParams pp;
-    for (int i = 0; i < 7; ++i) pp.bz[i] = g.bz[i];
+    for (int i = 0; i < kMaxC; ++i) pp.bz[i] = g.bz[i];
     pp.g0 = g.g0; pp.g1 = g.g1; pp.g2 = g.g2; pp.g3 = g.g3;
     pp.e0 = g.e0; pp.e1 = g.e1; pp.e2 = g.e2; pp.e3 = g.e3;
     return pp;
@@ -1838,6 +1845,7 @@ static int retract_F(const Geom& g, const Work& w, const void* U, const void* Xi
         case 1: return expr_tmpl(1);               \
         case 2: return expr_tmpl(2);               \
         case 3: return expr_tmpl(3);               \
+        case 4: return expr_tmpl(4);               \
         default: return SBEC_ERR_ARG;              \
     }
 

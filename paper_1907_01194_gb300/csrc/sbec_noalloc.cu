@@ -91,7 +91,7 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
                                    void* cuda_stream) {
     if (!prob || !X || !E) return SBEC_ERR_ARG;
     const sbec_problem& P = *prob;
-    if (P.F < 1 || P.F > 3 || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
+    if (P.F < 1 || P.F > sbec::kMaxF || P.dim < 1 || P.dim > 3) return SBEC_ERR_ARG;
     if (P.precision != SBEC_FP64) return SBEC_ERR_ARG;
     if (!(fabs(P.M) < (double)P.F)) return SBEC_ERR_ARG;
     for (int ax = 0; ax < 3; ++ax) {
@@ -123,7 +123,7 @@ extern "C" int sbec_energy_noalloc(const sbec_problem* prob, const double* V, co
     }
     g.G = (long long)P.n[0] * P.n[1] * P.n[2];
     g.dV = dV; g.invG = 1.0 / (double)g.G; g.M = P.M;
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < sbec::kMaxC; ++i) {
         const double l = (double)(P.F - i);
         g.bz[i] = (i < g.C) ? (-P.p * l + P.q * l * l) : 0.0;
     }

@@ -185,22 +185,78 @@ def paper_spin1_3d(M: float, n: int = 256) -> Workload:
                     beta=(880.0, -4.1, 0.0, 0.0), M=M, lattice_amp=100.0, lattice_k=np.pi / 2)
 
 
-def paper_spinor(w: Workload) -> np.ndarray:
-    """The paper's initial spinor U (Sec. 7) for the interaction type of w: spin-1
-    ferromagnetic (beta1 <= 0) or antiferromagnetic, spin-2 nematic."""
+# The paper's spin-2 cases (Sec. 7.2): I ferromagnetic, II antiferromagnetic (nematic
+# ground state), III cyclic
+SPIN2_BETA = {1: (130.6, -25.4, -125.3, 0.0), 2: (243.0, 12.1, -13.0, 0.0), 3: (183.9, 26.8, 134.7, 0.0)}
+# and spin-3 cases (Sec. 7.3)
+SPIN3_BETA = {1: (100.0, 1.0, -10.0, -1.0), 2: (100.0, 1.0, 10.0, 1.0)}
+
+
+def paper_spin2_2d_case(case: int, M: float, n: int = 256) -> Workload:
+    """Sec. 7.2, spin-2 2D case I/II/III: V = |x|^2/2 + 10 sum sin^2(pi x_i / 2), box
+    [-8,8]^2, n = 2^8 per axis on the finest mesh."""
+    return Workload(f"paper_spin2_2d_case{case}_n{n}", F=2, n=(n, n), lo=(-8.0, -8.0), hi=(8.0, 8.0),
+                    beta=SPIN2_BETA[case], M=M, lattice_amp=10.0, lattice_k=np.pi / 2)
+
+
+def paper_spin2_3d_case(case: int, M: float, n: int | None = None) -> Workload:
+    """Sec. 7.2, spin-2 3D case I/II/III: V = |x|^2/2 + 100 sum sin^2(pi x_i / 2); case I
+    on [-8,8] x [-16,16] x [-16,16] with n = 2^7, cases II and III on [-16,16]^3 with
+    n = 2^8 per axis."""
+    if case == 1:
+        n = n or 128
+        lo, hi = (-8.0, -16.0, -16.0), (8.0, 16.0, 16.0)
+    else:
+        n = n or 256
+        lo, hi = (-16.0,) * 3, (16.0,) * 3
+    return Workload(f"paper_spin2_3d_case{case}_n{n}", F=2, n=(n, n, n), lo=lo, hi=hi, beta=SPIN2_BETA[case], M=M,
+                    lattice_amp=100.0, lattice_k=np.pi / 2)
+
+
+def paper_spin3_2d(case: int, M: float, n: int = 256) -> Workload:
+    """Sec. 7.3, spin-3 2D case I/II: V = |x|^2/2 + 10 sum sin^2(pi x_i / 2), box [-8,8]^2,
+    n = 2^8 per axis."""
+    return Workload(f"paper_spin3_2d_case{case}_n{n}", F=3, n=(n, n), lo=(-8.0, -8.0), hi=(8.0, 8.0),
+                    beta=SPIN3_BETA[case], M=M, lattice_amp=10.0, lattice_k=np.pi / 2)
+
+
+def paper_spin3_3d(case: int, M: float, n: int = 128) -> Workload:
+    """Sec. 7.3, spin-3 3D case I/II: V = |x|^2/2 + 100 sum sin^2(pi x_i / 2), box
+    [-8,8]^3, n = 2^7 per axis."""
+    return Workload(f"paper_spin3_3d_case{case}_n{n}", F=3, n=(n, n, n), lo=(-8.0,) * 3, hi=(8.0,) * 3,
+                    beta=SPIN3_BETA[case], M=M, lattice_amp=100.0, lattice_k=np.pi / 2)
+
+
+def paper_spinor(w: Workload, seed: int = 0) -> np.ndarray:
+    """The paper's initial spinor U (Sec. 7) for the interaction type of w.
+
+    spin-1: ferromagnetic (beta1 <= 0) or antiferromagnetic; spin-2: ferromagnetic
+    (beta1 < 0, beta2 > 20 beta1), nematic (beta2 < 0, beta2 < 20 beta1) or cyclic
+    (beta1 > 0, beta2 > 0); spin-3: "a random vector", drawn here as 7 uniform
+    numbers in [0, 1) from numpy's PCG64 with the given seed."""
     M = w.M
     if w.F == 1 and w.beta[1] <= 0.0:
         return np.array([np.sqrt(1.0 + 3.0 * M) / 2.0, np.sqrt((1.0 - M) / 2.0), np.sqrt(1.0 - M) / 2.0])
     if w.F == 1:
         return np.array([np.sqrt((1.0 + M) / 2.0), 0.0, np.sqrt((1.0 - M) / 2.0)])
-    if w.F == 2 and w.beta[2] < 0.0 and w.beta[2] < 20.0 * w.beta[1]:
-        return np.array([np.sqrt(2.0 + M) / 2.0, 0.0, 0.0, 0.0, np.sqrt(2.0 - M) / 2.0])
+    if w.F == 2:
+        b1, b2 = w.beta[1], w.beta[2]
+        if b1 < 0.0 and b2 > 20.0 * b1:
+            m1, m2 = np.sqrt(2.0 + M), np.sqrt(2.0 - M)
+            return np.array([m1 ** 4 / 16.0, m1 ** 3 * m2 / 8.0, np.sqrt(6.0) * m1 ** 2 * m2 ** 2 / 16.0,
+                             m1 * m2 ** 3 / 8.0, m2 ** 4 / 16.0])
+        if b2 < 0.0 and b2 < 20.0 * b1:
+            return np.array([np.sqrt(2.0 + M) / 2.0, 0.0, 0.0, 0.0, np.sqrt(2.0 - M) / 2.0])
+        if b1 > 0.0 and b2 > 0.0:
+            return np.array([np.sqrt((M + 1.0) / 3.0), 0.0, 0.0, np.sqrt((2.0 - M) / 3.0), 0.0])
+    if w.F == 3:
+        return np.random.Generator(np.random.PCG64(seed)).uniform(0.0, 1.0, 7)
     raise ValueError("no initial spinor of the paper for this case")
 
 
-def paper_initial(w: Workload) -> np.ndarray:
+def paper_initial(w: Workload, seed: int = 0) -> np.ndarray:
     """The paper's initial data U phi_0 (Sec. 7) with phi_0 = pi^{-d/4} exp(-|x|^2/2),
-    scaled by sqrt(dV); complex128, (C,) + w.shape."""
+    scaled by sqrt(dV); complex128, (C,) + w.shape (seed: the spin-3 random spinor)."""
     axes = grid_axes(w)
     r2 = np.zeros(w.shape)
     for i, x in enumerate(axes):
@@ -208,7 +264,7 @@ def paper_initial(w: Workload) -> np.ndarray:
         sh[w.dim - 1 - i] = w.n[i]
         r2 = r2 + (x ** 2).reshape(sh)
     phi0 = np.pi ** (-w.dim / 4.0) * np.exp(-r2 / 2.0)
-    U = paper_spinor(w)
+    U = paper_spinor(w, seed)
     return (np.sqrt(w.dV) * U.reshape((w.C,) + (1,) * w.dim) * phi0[None]).astype(np.complex128)
 
 

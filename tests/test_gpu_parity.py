@@ -42,6 +42,9 @@ CASES = [
     _wl(1, (1024,), 20.0, 0.4, (300.0, 2.0, 0, 0)),                       # longest axis
     _wl(2, (512, 4), 12.0, 0.3, (80.0, 2.0, -1.0, 0)),                     # long x rows in 2D
     _wl(1, (4, 8, 512), 6.0, 0.1, (40.0, 1.0, 0, 0)),                      # long strided axis
+    _wl(4, (128,), 8.0, 1.3, (60.0, -1.5, 4.0, 0), p=0.1, q=0.05),        # spin-4, 1D
+    _wl(4, (32, 16), 6.0, 2.1, (80.0, 1.0, -3.0, 0), lattice=5.0),        # spin-4, 2D
+    _wl(4, (16, 8, 16), 6.0, 0.5, (120.0, -2.0, 6.0, 0)),                 # spin-4, 3D
 ]
 
 
@@ -82,7 +85,7 @@ def test_fp64_energy_grad_hess_parity(w, dev):
 
 
 @pytest.mark.parametrize("kind", [1, 2, 3])
-@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[6]], ids=lambda w: w.name)
+@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[6], CASES[11]], ids=lambda w: w.name)
 def test_fp64_retraction_parity(w, kind, dev):
     sbec = _sbec()
     P, u, Xf, Zf = case_inputs(w)
@@ -103,7 +106,7 @@ def test_fp64_retraction_parity(w, kind, dev):
             assert abs(got @ got - 1) < 1e-12 and abs(got @ (Gm * got) - w.M) < 1e-12
 
 
-@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5]], ids=lambda w: w.name)
+@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[12]], ids=lambda w: w.name)
 def test_mixed_precision_bound(w, dev):
     sbec = _sbec()
     P, u, Xf, Zf = case_inputs(w)

@@ -42,6 +42,8 @@ CASES = [
                 beta=(60.0, 2.0, -3.0, 0.0), M=0.4, lattice_amp=3.0, lattice_k=math.pi / 2), 1e-9),
     (W.Workload("s3_1d_128", F=3, n=(128,), lo=(-8.0,), hi=(8.0,),
                 beta=(80.0, -1.0, 4.0, 1.0), M=0.6), 1e-9),
+    (W.Workload("s4_2d_32", F=4, n=(32, 32), lo=(-6.0, -6.0), hi=(6.0, 6.0),
+                beta=(60.0, -1.0, 3.0, 0.0), M=1.2, lattice_amp=2.0, lattice_k=math.pi / 2), 1e-9),
 ]
 
 

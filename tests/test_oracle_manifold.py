@@ -19,7 +19,7 @@ def _case(F, n=(32,), M=0.3, seed=3):
     return w, P, u
 
 
-@pytest.mark.parametrize("F,M", [(1, 0.3), (2, 0.0), (2, 1.2), (3, 0.7)])
+@pytest.mark.parametrize("F,M", [(1, 0.3), (2, 0.0), (2, 1.2), (3, 0.7), (4, 2.2)])
 def test_projection_tangent_idempotent(F, M):
     w, P, u = _case(F, M=M)
     Gm = O.gamma_weights(P)
@@ -57,7 +57,7 @@ def test_riemannian_hessian_matches_connection(F, M):
 
 
 @pytest.mark.parametrize("kind", [1, 2, 3])
-@pytest.mark.parametrize("F,M", [(1, 0.5), (2, 0.0), (2, 1.3), (3, 0.2), (3, 2.5)])
+@pytest.mark.parametrize("F,M", [(1, 0.5), (2, 0.0), (2, 1.3), (3, 0.2), (3, 2.5), (4, 0.4)])
 def test_retraction_constraints_and_axioms(kind, F, M):
     w, P, u = _case(F, n=(32,), M=M)
     Gm = O.gamma_weights(P)

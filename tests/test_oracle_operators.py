@@ -19,7 +19,7 @@ def crandn(*shape):
 
 # ---------------------------------------------------------------- Sec. 2 matrices
 
-@pytest.mark.parametrize("F", [1, 2, 3])
+@pytest.mark.parametrize("F", [1, 2, 3, 4, 5])
 def test_spin_algebra(F):
     fx, fy, fz = O.spin_matrices(F)
     for f in (fx, fy, fz):
@@ -27,6 +27,32 @@ def test_spin_algebra(F):
     assert np.allclose(fx @ fy - fy @ fx, 1j * fz, atol=1e-14)
     assert np.allclose(fy @ fz - fz @ fy, 1j * fx, atol=1e-14)
     assert np.allclose(fx @ fx + fy @ fy + fz @ fz, F * (F + 1) * np.eye(2 * F + 1), atol=1e-13)
+
+
+@pytest.mark.parametrize("F", [1, 2, 3])
+def test_general_spin_matrices_are_the_printed_ones(F):
+    # the construction used for F >= 4 reproduces the matrices printed in Sec. 2
+    for a, b in zip(O.spin_matrices_general(F), O.spin_matrices(F)):
+        assert np.allclose(a, b, atol=1e-15)
+
+
+def _rotation(F, theta, axis):
+    # exp(-i theta f_axis) of the printed / general spin matrices
+    f = O.spin_matrices(F)[axis]
+    w, V = np.linalg.eigh(f)
+    return V @ np.diag(np.exp(-1j * theta * w)) @ V.conj().T
+
+
+@pytest.mark.parametrize("F", [2, 3, 4, 5])
+def test_singlet_pair_is_rotation_invariant(F):
+    # A00 = Phi^T A Phi is the amplitude of the total-spin-0 pair: a spin rotation
+    # R = exp(-i theta f) leaves it unchanged (R^T A R = A), and the matrices of
+    # F = 2, 3 are the printed ones
+    A = O.singlet_matrix(F)
+    for axis, th in ((0, 0.7), (1, -1.3), (2, 2.1)):
+        R = _rotation(F, th, axis)
+        assert np.allclose(R.T @ A @ R, A, atol=1e-12)
+    assert abs(np.linalg.norm(A) - 1.0) < 1e-14
 
 
 def test_spin1_explicit_F():
@@ -178,6 +204,10 @@ def _gaussian_energy_closed_form(F, d, U, beta, p, q, lattice_amp, lattice_k):
         if F == 2:
             A2 = abs((2 * u[2] * u[-2] - 2 * u[1] * u[-1] + u[0] ** 2) / math.sqrt(5)) ** 2
             Q2 = 0.0
+        elif F >= 4:
+            # singlet pair amplitude sum_l (-1)^(F-l) u_l u_-l / sqrt(2F+1); no quintet term
+            A2 = abs(sum((-1) ** (F - l) * u[l] * u[-l] for l in ls) / math.sqrt(2 * F + 1)) ** 2
+            Q2 = 0.0
         else:
             r21 = math.sqrt(21)
             A2 = abs((2 * u[3] * u[-3] - 2 * u[2] * u[-2] + 2 * u[1] * u[-1] - u[0] ** 2)
@@ -194,7 +224,7 @@ def _gaussian_energy_closed_form(F, d, U, beta, p, q, lattice_amp, lattice_k):
 
 
 @pytest.mark.parametrize("F,n,L", [(1, (128,), 16.0), (2, (64, 64), 8.0), (3, (128,), 16.0),
-                                   (3, (64, 64, 64), 8.0)])
+                                   (3, (64, 64, 64), 8.0), (4, (64, 64), 8.0), (5, (128,), 16.0)])
 def test_energy_gaussian_closed_form(F, n, L):
     d = len(n)
     beta = (37.0, -3.0, 5.0, 2.5)
@@ -220,7 +250,7 @@ def _fd_case(F, n, beta, seed):
     return P, X, D
 
 
-@pytest.mark.parametrize("F", [1, 2, 3])
+@pytest.mark.parametrize("F", [1, 2, 3, 4])
 @pytest.mark.parametrize("term", [0, 1, 2, 3, None])
 def test_gradient_central_fd(F, term):
     beta = (40.0, -3.0, 6.0, -2.0) if term is None else tuple(25.0 * (i == term) for i in range(4))
@@ -231,7 +261,7 @@ def test_gradient_central_fd(F, term):
     assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
 
 
-@pytest.mark.parametrize("F", [1, 2, 3])
+@pytest.mark.parametrize("F", [1, 2, 3, 4])
 @pytest.mark.parametrize("term", [0, 1, 2, 3, None])
 def test_hessvec_central_fd_and_symmetry(F, term):
     beta = (40.0, -3.0, 6.0, -2.0) if term is None else tuple(25.0 * (i == term) for i in range(4))
@@ -248,7 +278,7 @@ def test_hessvec_central_fd_and_symmetry(F, term):
 
 def test_energy_symmetry_flip_components():
     # Sec. 4: with p = 0, E is invariant under phi_l <-> phi_{-l}
-    for F in (1, 2, 3):
+    for F in (1, 2, 3, 4):
         w = small_workload(F, (32,), beta=(30.0, -2.0, 4.0, 1.5), q=0.4)
         P = oracle_problem(w)
         X = O.to_matrix(P, W.random_fields((P.C,) + P.shape, 5, 0.1))

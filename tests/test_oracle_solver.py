@@ -41,7 +41,7 @@ def _scalar_ground_energy(n, L, V, beta0):
     return 0.5 * x @ Lm @ x + x @ (V * x) + beta0 / (2 * h) * np.sum(x ** 4)
 
 
-@pytest.mark.parametrize("F,n,L,M", [(1, (64,), 8.0, 0.3), (3, (64,), 8.0, 1.4)])
+@pytest.mark.parametrize("F,n,L,M", [(1, (64,), 8.0, 0.3), (3, (64,), 8.0, 1.4), (4, (64,), 8.0, 2.5)])
 def test_harmonic_ground_state_is_d_over_2(F, n, L, M):
     w = small_workload(F, n, L=L, beta=(0.0, 0.0, 0.0, 0.0), M=M)
     P = oracle_problem(w)
@@ -67,7 +67,7 @@ def test_harmonic_gaussian_spinor_is_stationary(F, n, L, M):
     assert np.linalg.norm(O.rgrad(P, u)) < 1e-9
 
 
-@pytest.mark.parametrize("F,M", [(1, 0.2), (1, 0.7), (2, 0.3), (2, 1.2)])
+@pytest.mark.parametrize("F,M", [(1, 0.2), (1, 0.7), (2, 0.3), (2, 1.2), (4, 1.5)])
 def test_reduces_to_scalar_gpe(F, M):
     # beta1 = beta2 = beta3 = 0, p = q = 0: E_g does not depend on M and equals the
     # scalar ground energy with the same beta0 (Sec. 2, M = +-F remark)
