@@ -186,6 +186,26 @@ int sbec_solve(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* works
 int sbec_solve_batch(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* workspace, size_t workspace_bytes,
                      sbec_stats* stats);
 
+/* Device-driven solve (Algorithm 1 as one CUDA graph): the solve of every
+ * instance of nh handles (single or batch handles of one precision on one
+ * device, e.g. the grid-size classes of an uneven sweep), captured once and run
+ * as ONE graph launch.  The decisions sbec_solve_batch takes on the host (RGBB
+ * step and nonmonotone search, end of the modified CG, the direction of the
+ * Newton step, the curvilinear search, the ratio test and the sigma update) are
+ * taken per instance by one-block control kernels in the same formulas; the
+ * loops are conditional WHILE nodes whose conditions those kernels set, and the
+ * handles are parallel branches of the graph.  The host reads the scalar blocks
+ * once, after the graph.  X[i]: device array of handle i (overwritten with its
+ * ground states); workspaces[i]: at least sbec_solve_workspace_bytes of handle
+ * i; stats[i]: B_i entries.  loop_cap: executions of any loop body of a branch
+ * before the branch stops with SBEC_ERR_TIMEOUT (0: 10^6).  Returns SBEC_OK,
+ * SBEC_ERR_NOCONV (some instance above the tolerance), SBEC_ERR_TIMEOUT or an
+ * error.  Not available while sbec_profile is on (event timing cannot be
+ * captured).  Synchronises the handles' streams. */
+int sbec_solve_graph(sbec_handle* const* handles, int nh, void* const* X, const sbec_solve_opts* opts,
+                     void* const* workspaces, const size_t* workspace_bytes, long long loop_cap,
+                     sbec_stats* const* stats);
+
 /* Mixed-precision solve with FP64 refinement: X (complex128, device) is cast to
  * float, solved on h32 (precision SBEC_MIXED, same problem and stream as h64)
  * to max(tol_mixed, opts->tol) or at most 300 iterations, cast back, projected

@@ -639,6 +639,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_spass2(const SA
     for (int j2 = 0; j2 < N2; ++j2) dst[(long long)(q + N1 * j2) * es] = v[j2];
 }
 
+}  // namespace sbec
+
+// the TMA variant of the strided pass (uses SArgs, the pass modes and the finalize bodies above)
+#include "sbec_tma.cuh"
+
+namespace sbec {
+
 // x pass of 2D / 3D problems (X_FWD, X_FWD_EPW, X_INV): rpb grid rows of all C
 // components; pencil p = row group * C + component, thread (p, q) with
 // q = tid mod N1 (threads with p >= P only join the barriers and sums).
@@ -1624,6 +1631,110 @@ static int launch_s(const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA strided passes (FP32 single-instance fields, pass axis of 128 or 256 points)
+// ---------------------------------------------------------------------------
+// cuTensorMapEncodeTiled fetched from the driver at run time (the library links
+// the runtime only); null when the driver does not provide it.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tma_encoder() {
+    static std::atomic<int> state{0};            // 0 unknown, 1 available, -1 unavailable
+    static std::atomic<EncodeTiledFn> fn{nullptr};
+    int st = state.load(std::memory_order_acquire);
+    if (st == 0) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && p) {
+            fn.store(reinterpret_cast<EncodeTiledFn>(p), std::memory_order_release);
+            st = 1;
+        } else {
+            cudaGetLastError();
+            st = -1;
+        }
+        state.store(st, std::memory_order_release);
+    }
+    return st == 1 ? fn.load(std::memory_order_acquire) : nullptr;
+}
+
+// The field at `base` as a 4D float tensor [C][n_z][n_y][2 n_x] with a box of one
+// tile of the pass along `axis` (2W floats along x, the whole axis).
+static bool tma_map(CUtensorMap* m, const void* base, const Geom& g, int axis) {
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t nx2 = 2ull * (cuuint64_t)g.n[0];
+    const cuuint64_t dims[4] = {nx2, (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)g.C};
+    const cuuint64_t strides[3] = {nx2 * 4, nx2 * g.n[1] * 4, nx2 * g.n[1] * g.n[2] * 4};
+    const cuuint32_t box[4] = {2u * kTmaW, axis == 1 ? (cuuint32_t)g.n[1] : 1u, axis == 2 ? (cuuint32_t)g.n[2] : 1u,
+                               1u};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the pass runs on the TMA kernel: FP32, one instance, the built-in tile width,
+// a pass axis of 128 or 256 points and x a multiple of the tile width
+template <typename T>
+static bool tma_pass(const Geom& g, int axis) {
+    if (sizeof(T) != 4 || g.B != 1 || g.nl != 1 || g.imap || g.dim < 2) return false;
+    if (g.n[axis] != 128 && g.n[axis] != 256) return false;
+    if (g.n[0] % kTmaW != 0) return false;
+    if (g.tune.s_pencils[axis] != 0 && g.tune.s_pencils[axis] != kTmaW) return false;
+    return tma_encoder() != nullptr;
+}
+
+template <int MODE, int LOGN>
+static int launch_tma_n(const Geom& g, const SArgs& a, const Work& w, cudaStream_t s) {
+    auto kern = k_spass_tma<MODE, LOGN>;
+    constexpr size_t smem = tma_smem_bytes<LOGN>();
+    constexpr int nth = kTmaW * Split2<LOGN>::N1;
+    static size_t granted = 0;
+    if (int st = ensure_smem(kern, smem, granted)) return st;
+    static std::atomic<int> occ{0};
+    int per_sm = occ.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nth, smem) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        occ.store(per_sm, std::memory_order_relaxed);
+    }
+    CUtensorMap mi, mo;
+    if (!tma_map(&mi, a.in, g, a.axis)) return SBEC_ERR_CUDA;
+    if (!tma_map(&mo, a.out ? a.out : a.in, g, a.axis)) return SBEC_ERR_CUDA;
+    TmaArgs ta;
+    ta.s = a;
+    ta.ntiles = (long long)g.C * a.nouter * a.ntx;
+    ta.status = w.scal;
+    long long grid = (long long)w.num_sms * per_sm;
+    if (grid > ta.ntiles) grid = ta.ntiles;
+    ProfScope ps(w.prof, SKid<MODE>::v, s);
+    kern<<<(int)grid, nth, smem, s>>>(ta, mi, mo);
+    SBEC_LAUNCH_CHECK();
+    return SBEC_OK;
+}
+
+// strided pass along a.axis: the TMA kernel where it applies, else the
+// two-level / Stockham kernels
+template <typename T, int MODE>
+static int launch_pass(const Geom& g, const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
+    if (tma_pass<T>(g, a.axis)) {
+        if (a.W != kTmaW) {
+            SArgs b = a;
+            b.W = kTmaW;
+            b.ntx = g.n[0] / kTmaW;
+            return g.n[a.axis] == 256 ? launch_tma_n<MODE, 8>(g, b, w, s) : launch_tma_n<MODE, 7>(g, b, w, s);
+        }
+        return g.n[a.axis] == 256 ? launch_tma_n<MODE, 8>(g, a, w, s) : launch_tma_n<MODE, 7>(g, a, w, s);
+    }
+    return launch_s<T, MODE>(c, a, w, s);
+}
+
 // launch of an elementwise / finalize kernel with bookkeeping
 #define SBEC_LAUNCH(kid, kern, grid, block, ...)            \
     do {                                                    \
@@ -1699,15 +1810,15 @@ static int middle_passes(const Geom& g, const Work& w, cudaStream_t s) {
     const int d = g.dim;
     if (d == 2) {
         const SCfg c = scfg<T>(g, 1, w.num_sms);
-        return launch_s<T, S_K2>(c, sargs<T>(g, c, 1, w.work, w.work, nullptr), w, s);
+        return launch_pass<T, S_K2>(g, c, sargs<T>(g, c, 1, w.work, w.work, nullptr), w, s);
     }
     // d == 3
     const SCfg cy = scfg<T>(g, 1, w.num_sms), cz = scfg<T>(g, 2, w.num_sms);
-    int st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+    int st = launch_pass<T, S_FWD>(g, cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
     if (st) return st;
-    st = launch_s<T, S_K2>(cz, sargs<T>(g, cz, 2, w.work, w.work, nullptr), w, s);
+    st = launch_pass<T, S_K2>(g, cz, sargs<T>(g, cz, 2, w.work, w.work, nullptr), w, s);
     if (st) return st;
-    return launch_s<T, S_INV>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+    return launch_pass<T, S_INV>(g, cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
 }
 
 template <typename T, int F>
@@ -1769,7 +1880,7 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
     const int axis = g.dim == 2 ? 1 : 2;
     if (g.dim == 3) {
         const SCfg cy = scfg<T>(g, 1, w.num_sms);
-        st = launch_s<T, S_FWD>(cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
+        st = launch_pass<T, S_FWD>(g, cy, sargs<T>(g, cy, 1, w.work, w.work, nullptr), w, s);
         if (st) return st;
     }
     const SCfg cl = scfg<T>(g, axis, w.num_sms);
@@ -1777,7 +1888,7 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
     a.fe.on = 1;
     a.fe.pa = w.partA; a.fe.na_tot = c.nblk; a.fe.na_inst = c.nblk_inst;
     a.fe.scal0 = w.scal;
-    return launch_s<T, S_PARSEVAL>(cl, a, w, s);
+    return launch_pass<T, S_PARSEVAL>(g, cl, a, w, s);
 }
 
 template <typename T, int F>
@@ -2054,7 +2165,8 @@ Tune Ops<T>::resolved(const Geom& g, int num_sms) {
     Tune t{};
     t.x_rows = xcfg<T>(g).rpb;
     for (int ax = 1; ax < g.dim; ++ax) {
-        t.s_pencils[ax] = scfg<T>(g, ax, num_sms).W;
+        // the TMA pass takes the built-in choice where it applies (its tile is kTmaW wide)
+        t.s_pencils[ax] = tma_pass<T>(g, ax) ? kTmaW : scfg<T>(g, ax, num_sms).W;
         t.s_split[ax] = g.tune.s_split[ax] > 0 ? g.tune.s_split[ax] : 1;
     }
     t.elem_per_sm = g.tune.elem_per_sm > 0 ? g.tune.elem_per_sm : 8;

@@ -1187,3 +1187,620 @@ int sbec_solve_cascadic_mixed(sbec_handle* const* levels64, sbec_handle* const* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Device-driven solve (Algorithm 1 as one CUDA graph).  Every decision the
+// lock-step batch solver takes on the host -- the RGBB step and its nonmonotone
+// search, the modified CG's end, the direction of Eq. (xi), the curvilinear
+// search, the ratio test and the sigma update -- is taken per instance by
+// one-block control kernels on the device, in the same formulas and order.  The
+// loops are conditional WHILE nodes of the graph whose condition the control
+// kernels set (cudaGraphSetConditional); kernels of instances outside the
+// current sub-phase return at once through the instances' S_SKIP flags.  Several
+// batch handles (e.g. the grid-size classes of an uneven sweep) are parallel
+// branches of the same graph, so one launch solves all of them; the host reads
+// the scalar blocks once, after the graph.  Every loop counts its body
+// executions and stops at a cap, recording SBEC_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+namespace {
+
+// per-instance state of the device-driven solve (scalar-block slots after the
+// solver slots of the host-driven solvers)
+enum {
+    DS_E = 64, DS_GN, DS_CK, DS_QK, DS_T, DS_SLOPE, DS_EZ, DS_BT, DS_ACT, DS_TR, DS_K, DS_PREV,
+    DS_SIGHAT, DS_SIGFLOOR, DS_MZ, DS_CGON, DS_NEG, DS_HD, DS_SEST, DS_OUTER, DS_INNER, DS_RGBBIT,
+    DS_NGRAD, DS_NENERGY, DS_NHVP, DS_ERR, DS_DOM, DS_LOOP0 /* 5 loop counters, instance 0 */
+};
+static_assert(int(DS_LOOP0) + 5 <= int(sbec::S_COUNT), "device solver slots exceed the scalar block");
+
+enum GPhase {
+    G_INIT, G_RGBB_GRAD, G_RGBB_LS, G_RGBB_ACC, G_RGBB_END, G_ARNT_E, G_ARNT_INIT, G_ARNT_TOP, G_ARNT_CG0,
+    G_CG_ANY, G_ARNT_DIR, G_ARNT_TAU, G_ARNT_SLOPE, G_ARNT_LS0, G_ARNT_LS, G_ARNT_E2, G_ARNT_ACC, G_ARNT_END,
+    G_FINAL
+};
+
+struct GCtl {
+    int B;
+    double tol_r, tol;          // RGBB tolerance (warm start or final), ARNT tolerance
+    long long maxit_r, maxit;
+    double eps;                 // unit roundoff of the handle's precision (rounding floor)
+    long long cap;              // loop-body executions per loop before SBEC_ERR_TIMEOUT
+};
+
+// status of instance b after the latest kernels: 0, DOMAIN (cleared, reported
+// back) or a fatal code (recorded in DS_ERR)
+__device__ __forceinline__ int take_status(double* sc) {
+    const int st = (int)sc[SBEC_S_STATUS];
+    sc[SBEC_S_STATUS] = 0.0;
+    if (st != 0 && st != SBEC_ERR_DOMAIN && sc[DS_ERR] == 0.0) sc[DS_ERR] = double(st);
+    return st;
+}
+
+// One block over all instances of a branch; thread 0 sets the loop conditions.
+__global__ void __launch_bounds__(1024) k_gctl(double* scal0, const GCtl c, int phase, cudaGraphConditionalHandle h1,
+                                               cudaGraphConditionalHandle h2, int loop) {
+    __shared__ int any1, any2, over;
+    if (threadIdx.x == 0) { any1 = 0; any2 = 0; over = 0; }
+    __syncthreads();
+    for (int b = threadIdx.x; b < c.B; b += blockDim.x) {
+        double* sc = scal0 + (size_t)b * sbec::S_COUNT;
+        const double noise = 100.0 * c.eps * fmax(1.0, fabs(sc[DS_E]));
+        switch (phase) {
+            case G_INIT: {
+                const int st = take_status(sc);
+                if (st == SBEC_ERR_DOMAIN && sc[DS_ERR] == 0.0) sc[DS_ERR] = double(SBEC_ERR_DOMAIN);
+                sc[DS_E] = sc[SBEC_S_ENERGY];
+                sc[DS_CK] = sc[DS_E]; sc[DS_QK] = 1.0;
+                sc[DS_ACT] = sc[DS_ERR] == 0.0 ? 1.0 : 0.0;
+                sc[DS_K] = 0.0; sc[DS_PREV] = 0.0;
+                sc[DS_NENERGY] += 1.0;
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                if (sc[DS_ACT] != 0.0) atomicOr(&any1, 1);
+                break;
+            }
+            case G_RGBB_GRAD: {
+                sc[DS_NGRAD] += 1.0;
+                take_status(sc);
+                if (sc[DS_ERR] != 0.0) sc[DS_ACT] = 0.0;
+                const double gn = sqrt(sc[SBEC_S_RGRAD_NORM2]);
+                if (sc[DS_ACT] != 0.0) sc[DS_GN] = gn;
+                if (sc[DS_ACT] != 0.0 && (gn <= c.tol_r || sc[DS_K] == (double)c.maxit_r)) sc[DS_ACT] = 0.0;
+                const bool act = sc[DS_ACT] != 0.0;
+                if (act) {
+                    double gam = 1e-3;
+                    if (sc[DS_PREV] != 0.0) {
+                        const double sv = sc[SL_D0], vv = sc[SL_D0 + 1];
+                        gam = vv > 0.0 ? fabs(sv) / vv : 1e-3;
+                        gam = fmin(fmax(gam, 1e-10), 1e10);
+                    }
+                    sc[DS_T] = gam;
+                    sc[DS_SLOPE] = -gn * gn;
+                    sc[DS_EZ] = INFINITY;
+                    sc[DS_BT] = 0.0;
+                    atomicOr(&any1, 1);
+                }
+                sc[DS_TR] = act ? 1.0 : 0.0;
+                sc[SL_T] = act ? -sc[DS_T] : 0.0;
+                sc[sbec::S_SKIP] = act ? 0.0 : 1.0;
+                break;
+            }
+            case G_RGBB_LS: {
+                sc[DS_NENERGY] += 1.0;
+                const int st = take_status(sc);
+                if (sc[DS_TR] != 0.0) {
+                    const double Ez = (st == SBEC_ERR_DOMAIN) ? INFINITY : sc[SBEC_S_ENERGY];
+                    sc[DS_EZ] = Ez;
+                    const double t = sc[DS_T];
+                    if (sc[DS_ERR] != 0.0) {
+                        sc[DS_TR] = 0.0;
+                    } else if (Ez <= sc[DS_CK] + 1e-4 * t * sc[DS_SLOPE] || fabs(Ez - sc[DS_E]) <= noise) {
+                        sc[DS_TR] = 0.0;
+                    } else if (sc[DS_BT] < 10.0) {
+                        sc[DS_T] = 0.2 * t;
+                    } else {
+                        sc[DS_TR] = 0.0;
+                    }
+                    sc[DS_BT] += 1.0;
+                }
+                const bool tr = sc[DS_TR] != 0.0;
+                sc[SL_T] = (sc[DS_ACT] != 0.0) ? -sc[DS_T] : 0.0;
+                sc[sbec::S_SKIP] = tr ? 0.0 : 1.0;
+                if (tr) atomicOr(&any1, 1);
+                break;
+            }
+            case G_RGBB_ACC: {
+                if (sc[DS_ACT] != 0.0 && (!isfinite(sc[DS_EZ]) || sc[DS_ERR] != 0.0)) sc[DS_ACT] = 0.0;
+                sc[SL_ACT] = sc[DS_ACT];
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                break;
+            }
+            case G_RGBB_END: {
+                if (sc[DS_ACT] != 0.0) {
+                    sc[DS_E] = sc[DS_EZ];
+                    const double Qn = 0.85 * sc[DS_QK] + 1.0;
+                    sc[DS_CK] = (0.85 * sc[DS_QK] * sc[DS_CK] + sc[DS_E]) / Qn;
+                    sc[DS_QK] = Qn;
+                    sc[DS_RGBBIT] += 1.0;
+                    sc[DS_K] += 1.0;
+                    sc[DS_PREV] = 1.0;
+                    atomicOr(&any1, 1);
+                }
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_E: {
+                // RGBB over: every instance without a fatal error takes part in ARNT
+                sc[DS_NENERGY] += 1.0;
+                take_status(sc);
+                sc[DS_E] = sc[SBEC_S_ENERGY];
+                sc[DS_ACT] = sc[DS_ERR] == 0.0 ? 1.0 : 0.0;
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_INIT: {
+                sc[DS_NGRAD] += 1.0;
+                take_status(sc);
+                if (sc[DS_ERR] != 0.0) sc[DS_ACT] = 0.0;
+                sc[DS_GN] = sqrt(sc[SBEC_S_RGRAD_NORM2]);
+                sc[DS_SIGHAT] = 1.0; sc[DS_SIGFLOOR] = 0.0; sc[DS_K] = 0.0;
+                if (sc[DS_ACT] != 0.0 && (sc[DS_GN] <= c.tol || c.maxit == 0)) sc[DS_ACT] = 0.0;
+                if (sc[DS_ACT] != 0.0) atomicOr(&any1, 1);
+                break;
+            }
+            case G_ARNT_TOP: {
+                if (sc[DS_ACT] != 0.0 && (sc[DS_GN] <= c.tol || sc[DS_K] == (double)c.maxit)) sc[DS_ACT] = 0.0;
+                const bool act = sc[DS_ACT] != 0.0;
+                const double gn = sc[DS_GN];
+                if (act) {
+                    sc[SL_SIG] = fmax(sc[DS_SIGHAT] * gn, sc[DS_SIGFLOOR]);
+                    sc[SL_MAXIN] = gn > 1e-3 ? 100.0 : 300.0;
+                    sc[SL_STOP] = fmin(0.1, gn) * gn;
+                }
+                sc[sbec::S_SKIP] = act ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_CG0: {
+                const bool act = sc[DS_ACT] != 0.0;
+                const bool cg = act && sc[SL_RRA] > 0.0;
+                sc[DS_CGON] = cg ? 1.0 : 0.0;
+                sc[DS_NEG] = 0.0; sc[DS_HD] = 0.0; sc[DS_SEST] = -1.0;
+                sc[SL_CG] = cg ? 1.0 : 0.0;
+                sc[SL_J] = 0.0; sc[SL_SEST] = -1.0; sc[SL_CGNEG] = 0.0; sc[SL_CGHD] = 0.0;
+                sc[sbec::S_SKIP] = cg ? 0.0 : 1.0;
+                if (cg) atomicOr(&any1, 1);
+                break;
+            }
+            case G_CG_ANY: {
+                take_status(sc);
+                if (sc[DS_CGON] != 0.0 && sc[SL_CG] != 0.0) atomicOr(&any1, 1);
+                break;
+            }
+            case G_ARNT_DIR: {
+                const bool act = sc[DS_ACT] != 0.0;
+                if (sc[DS_CGON] != 0.0) {
+                    sc[DS_INNER] += sc[SL_J];
+                    sc[DS_NHVP] += sc[SL_J];
+                    sc[DS_NEG] = sc[SL_CGNEG] != 0.0 ? 1.0 : 0.0;
+                    sc[DS_HD] = sc[SL_CGHD] != 0.0 ? 1.0 : 0.0;
+                    sc[DS_SEST] = sc[SL_SEST];
+                }
+                sc[SL_NEG] = (act && sc[DS_NEG] != 0.0) ? 1.0 : 0.0;
+                sc[SL_HD] = (act && sc[DS_HD] != 0.0) ? 1.0 : 0.0;
+                sc[sbec::S_SKIP] = act ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_TAU: {
+                sc[SL_TAU] = sc[SL_HD] != 0.0 ? sc[SL_D0] / sc[SL_D0 + 1] : 0.0;
+                break;
+            }
+            case G_ARNT_SLOPE: {
+                const bool act = sc[DS_ACT] != 0.0;
+                double slope = sc[SL_D0];
+                const bool fix = act && (!(slope < 0.0) || !isfinite(slope));
+                if (fix) slope = -sc[DS_GN] * sc[DS_GN];
+                sc[DS_SLOPE] = slope;
+                sc[SL_NEG] = fix ? 1.0 : 0.0;
+                break;
+            }
+            case G_ARNT_LS0: {
+                const bool act = sc[DS_ACT] != 0.0;
+                sc[DS_T] = 1.0; sc[DS_MZ] = INFINITY; sc[DS_BT] = 0.0;
+                sc[DS_TR] = act ? 1.0 : 0.0;
+                sc[SL_T] = act ? 1.0 : 0.0;
+                sc[sbec::S_SKIP] = act ? 0.0 : 1.0;
+                if (act) atomicOr(&any1, 1);
+                break;
+            }
+            case G_ARNT_LS: {
+                sc[DS_NHVP] += 1.0;
+                const int st = take_status(sc);
+                if (sc[DS_TR] != 0.0) {
+                    const double mz = (st == SBEC_ERR_DOMAIN)
+                                          ? INFINITY
+                                          : sc[SL_MA] + 0.5 * sc[SL_MB] + 0.5 * sc[SL_SIG] * sc[SL_MA + 1];
+                    sc[DS_MZ] = mz;
+                    const double t = sc[DS_T];
+                    if (sc[DS_ERR] != 0.0 || mz <= 1e-4 * t * sc[DS_SLOPE] || fabs(mz) <= noise) {
+                        sc[DS_TR] = 0.0;
+                    } else if (sc[DS_BT] < 10.0) {
+                        sc[DS_T] = 0.2 * t;
+                    } else {
+                        sc[DS_TR] = 0.0;
+                    }
+                    sc[DS_BT] += 1.0;
+                }
+                const bool tr = sc[DS_TR] != 0.0;
+                sc[SL_T] = sc[DS_ACT] != 0.0 ? sc[DS_T] : 0.0;
+                sc[sbec::S_SKIP] = tr ? 0.0 : 1.0;
+                if (tr) atomicOr(&any1, 1);
+                break;
+            }
+            case G_ARNT_E2: {
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_ACC: {
+                sc[DS_NENERGY] += 1.0;
+                const int st = take_status(sc);
+                bool acc = false;
+                if (sc[DS_ACT] != 0.0) {
+                    const double Ez = (st == SBEC_ERR_DOMAIN) ? INFINITY : sc[SBEC_S_ENERGY];
+                    const double mz = sc[DS_MZ], E = sc[DS_E];
+                    double ratio;
+                    if (fabs(mz) <= noise && fabs(Ez - E) <= noise) ratio = 1.0;
+                    else ratio = (mz < 0.0 && isfinite(Ez)) ? (Ez - E) / mz : -1.0;
+                    acc = ratio >= 0.01 && sc[DS_ERR] == 0.0;
+                    if (acc) {
+                        sc[DS_E] = Ez;
+                        sc[DS_SIGHAT] *= (ratio >= 0.9) ? 0.2 : 1.0;
+                    } else {
+                        sc[DS_SIGHAT] *= 10.0;
+                    }
+                    sc[DS_SIGFLOOR] = sc[DS_SEST] >= 0.0 ? sc[DS_SEST] : 0.0;
+                    sc[DS_OUTER] += 1.0;
+                }
+                sc[SL_ACC] = acc ? 1.0 : 0.0;
+                sc[sbec::S_SKIP] = acc ? 0.0 : 1.0;
+                break;
+            }
+            case G_ARNT_END: {
+                if (sc[SL_ACC] != 0.0) {
+                    sc[DS_NGRAD] += 1.0;
+                    take_status(sc);
+                    sc[DS_GN] = sqrt(sc[SBEC_S_RGRAD_NORM2]);
+                }
+                if (sc[DS_ERR] != 0.0) sc[DS_ACT] = 0.0;
+                if (sc[DS_ACT] != 0.0) {
+                    sc[DS_K] += 1.0;
+                    if (sc[DS_SIGHAT] > 1e20) sc[DS_ACT] = 0.0;
+                }
+                // the next iteration's top test, so that the loop ends without an empty pass
+                if (sc[DS_ACT] != 0.0 && !(sc[DS_GN] <= c.tol || sc[DS_K] == (double)c.maxit)) atomicOr(&any1, 1);
+                sc[sbec::S_SKIP] = sc[DS_ACT] != 0.0 ? 0.0 : 1.0;
+                break;
+            }
+            case G_FINAL: {
+                sc[DS_NGRAD] += 1.0;
+                sc[sbec::S_SKIP] = 0.0;
+                break;
+            }
+            default:
+                break;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // loop bookkeeping: body executions of loop `loop` (instance 0's block)
+        if (loop >= 0) {
+            double* cnt = scal0 + DS_LOOP0 + loop;
+            cnt[0] += 1.0;
+            if (cnt[0] >= (double)c.cap) {
+                over = 1;
+                if (scal0[DS_ERR] == 0.0) scal0[DS_ERR] = double(SBEC_ERR_TIMEOUT);
+            }
+        }
+        if (h1) cudaGraphSetConditional(h1, (any1 && !over) ? 1u : 0u);
+        if (h2) cudaGraphSetConditional(h2, (any2 && !over) ? 1u : 0u);
+    }
+}
+
+// every instance's device-solver state back to zero (the launch of a solve)
+__global__ void k_gclear(double* scal0, int B) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * (sbec::S_COUNT - DS_E); i += gridDim.x * blockDim.x) {
+        const int b = i / (sbec::S_COUNT - DS_E), k = i % (sbec::S_COUNT - DS_E);
+        scal0[(size_t)b * sbec::S_COUNT + DS_E + k] = 0.0;
+    }
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+        scal0[(size_t)b * sbec::S_COUNT + sbec::S_SKIP] = 0.0;
+        scal0[(size_t)b * sbec::S_COUNT + SBEC_S_STATUS] = 0.0;
+    }
+}
+
+// Builds one branch (one handle) of the device-driven graph by stream capture.
+template <typename T>
+struct GraphBranch {
+    sbec_handle* h;
+    sbec::Geom g;
+    sbec::Work w;          // the handle's work area without the event profiler
+    sbec_solve_opts o;
+    GCtl ctl;
+    void* f[10];
+    void* Xdev;
+    cudaStream_t st[4] = {};   // capture streams by nesting depth
+    CgChunks<T>* cg = nullptr;
+    int err = SBEC_OK;
+
+    GraphBranch(sbec_handle* hh, const sbec_solve_opts& oo, void* ws, void* X, long long cap) : h(hh), g(hh->geom), w(hh->work), o(oo) {
+        w.prof = nullptr;
+        g.nl = hh->B;
+        g.imap = nullptr;
+        char* b = static_cast<char*>(ws);
+        for (int i = 0; i < 10; ++i) f[i] = b + (size_t)i * hh->field_bytes;
+        Xdev = X;
+        ctl.B = hh->B;
+        ctl.tol = o.tol;
+        ctl.tol_r = o.method == SBEC_RGBB ? o.tol : fmax(o.tol, o.rgbb_tol);
+        ctl.maxit_r = o.method == SBEC_RGBB ? o.maxit : o.rgbb_maxit;
+        ctl.maxit = o.maxit;
+        ctl.eps = sizeof(T) == 8 ? kEps : 1.1920928955078125e-07;
+        ctl.cap = cap;
+        for (auto& s : st)
+            if (!err && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) err = SBEC_ERR_CUDA;
+        cg = new CgChunks<T>(hh, 2, false);
+    }
+    ~GraphBranch() {
+        delete cg;
+        for (auto& s : st)
+            if (s) cudaStreamDestroy(s);
+    }
+
+#define GTRY(x) do { int e_ = (x); if (e_) return e_; } while (0)
+    int ctlk(cudaStream_t s, int phase, cudaGraphConditionalHandle h1 = 0, cudaGraphConditionalHandle h2 = 0,
+             int loop = -1) {
+        k_gctl<<<1, 1024, 0, s>>>(w.scal, ctl, phase, h1, h2, loop);
+        return cudaGetLastError() == cudaSuccess ? SBEC_OK : SBEC_ERR_CUDA;
+    }
+    int lin(cudaStream_t s, void* out, double ca, const void* A, double cb, const void* B, int ib = -1,
+            int guard = -1, const void* D1 = nullptr, const void* D2 = nullptr, int slot = SL_D0) {
+        Lin L;
+        L.out = out; L.A = A; L.B = B; L.ca = ca; L.cb = cb; L.ia = -1; L.ib = ib; L.ineg = -1;
+        L.D1 = D1; L.D2 = D2; L.guard = guard;
+        return Ops<T>::lincomb(g, w, L, slot, s);
+    }
+
+    // WHILE node on the stream capturing at `depth`: the body is captured on the
+    // stream of depth + 1 by body(stream); the handle is created before the node so
+    // that the kernel ahead of it (set_cond) can set its first value.
+    template <typename Body>
+    int while_node(int depth, cudaGraphConditionalHandle hnd, Body body) {
+        cudaStream_t s = st[depth], sb = st[depth + 1];
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t graph;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps) != cudaSuccess ||
+            cs != cudaStreamCaptureStatusActive)
+            return SBEC_ERR_CUDA;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp) != cudaSuccess) return SBEC_ERR_CUDA;
+        cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(sb, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+            cudaSuccess)
+            return SBEC_ERR_CUDA;
+        const int e = body(sb);
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(sb, &out);
+        if (e) return e;
+        if (ee != cudaSuccess) return SBEC_ERR_CUDA;
+        if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+            return SBEC_ERR_CUDA;
+        return SBEC_OK;
+    }
+    int handle_in(int depth, cudaGraphConditionalHandle* hnd) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t graph;
+        if (cudaStreamGetCaptureInfo(st[depth], &cs, nullptr, &graph, nullptr, nullptr, nullptr) != cudaSuccess ||
+            cs != cudaStreamCaptureStatusActive)
+            return SBEC_ERR_CUDA;
+        return cudaGraphConditionalHandleCreate(hnd, graph, 0, 0) == cudaSuccess ? SBEC_OK : SBEC_ERR_CUDA;
+    }
+
+    // Captures the whole solve of this handle on st[0] (already capturing).
+    int build() {
+        if (err) return err;
+        cudaStream_t s0 = st[0];
+        void *u = f[0], *up = f[1], *z = f[2], *gE = f[3], *rg = f[4], *rgp = f[5];
+        void *x = f[6], *r = f[7], *p = f[8], *Hp = f[9];
+        k_gclear<<<8, 256, 0, s0>>>(w.scal, h->B);
+        if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
+        // every work field starts at zero: the kernels that run for all instances (the
+        // BB dots before the first step, the direction dots) then only see finite values
+        if (cudaMemsetAsync(f[0], 0, 10 * h->field_bytes, s0) != cudaSuccess) return SBEC_ERR_CUDA;
+        if (cudaMemcpyAsync(u, Xdev, h->field_bytes, cudaMemcpyDeviceToDevice, s0) != cudaSuccess) return SBEC_ERR_CUDA;
+        if (o.project_initial) GTRY(Ops<T>::retract(g, w, u, u, 0.0, 1, u, s0));
+        GTRY(Ops<T>::energy(g, w, u, s0));
+        // ---- RGBB (warm start, or the whole solve) ----
+        cudaGraphConditionalHandle c_rgbb, c_rls;
+        GTRY(handle_in(0, &c_rgbb));
+        GTRY(ctlk(s0, G_INIT, c_rgbb));
+        GTRY(while_node(0, c_rgbb, [&](cudaStream_t s1) -> int {
+            GTRY(Ops<T>::grad(g, w, u, nullptr, rg, true, s1));
+            GTRY(Ops<T>::bbdots(g, w, u, up, rg, rgp, SL_D0, s1));
+            GTRY(handle_in(1, &c_rls));
+            GTRY(ctlk(s1, G_RGBB_GRAD, c_rls, 0, 0));
+            GTRY(while_node(1, c_rls, [&](cudaStream_t s2) -> int {
+                GTRY(Ops<T>::retract(g, w, u, rg, 1.0, o.retraction, z, s2, SL_T));
+                GTRY(Ops<T>::energy(g, w, z, s2));
+                return ctlk(s2, G_RGBB_LS, c_rls, 0, 1);
+            }));
+            GTRY(ctlk(s1, G_RGBB_ACC));
+            GTRY(lin(s1, up, 1.0, u, 0.0, nullptr, -1, SL_ACT));
+            GTRY(lin(s1, rgp, 1.0, rg, 0.0, nullptr, -1, SL_ACT));
+            GTRY(lin(s1, u, 1.0, z, 0.0, nullptr, -1, SL_ACT));
+            return ctlk(s1, G_RGBB_END, c_rgbb);
+        }));
+        if (o.method != SBEC_RGBB) {
+            // ---- ARNT (Algorithm 1, second loop) ----
+            k_unskip<<<(h->B + 127) / 128, 128, 0, s0>>>(w.scal, h->B);
+            if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
+            GTRY(Ops<T>::energy(g, w, u, s0));
+            GTRY(ctlk(s0, G_ARNT_E));
+            GTRY(Ops<T>::grad(g, w, u, gE, rg, true, s0));
+            cudaGraphConditionalHandle c_arnt, c_cg, c_ls;
+            GTRY(handle_in(0, &c_arnt));
+            GTRY(ctlk(s0, G_ARNT_INIT, c_arnt));
+            GTRY(while_node(0, c_arnt, [&](cudaStream_t s1) -> int {
+                GTRY(ctlk(s1, G_ARNT_TOP));
+                GTRY(lin(s1, x, 0.0, rg, 0.0, nullptr));
+                GTRY(lin(s1, r, -1.0, rg, 0.0, nullptr, -1, -1, r, nullptr, SL_RRA));
+                GTRY(lin(s1, p, 1.0, r, 0.0, nullptr));
+                GTRY(handle_in(1, &c_cg));
+                GTRY(ctlk(s1, G_ARNT_CG0, c_cg));
+                GTRY(while_node(1, c_cg, [&](cudaStream_t s2) -> int {
+                    GTRY(cg->launch(s2, u, p, Hp, x, r, 0));
+                    return ctlk(s2, G_CG_ANY, c_cg, 0, 2);
+                }));
+                GTRY(ctlk(s1, G_ARNT_DIR));
+                GTRY(lin(s1, x, -1.0, rg, 0.0, nullptr, -1, SL_NEG));
+                GTRY(Ops<T>::dot2(g, w, p, rg, p, Hp, SL_D0, s1));
+                GTRY(ctlk(s1, G_ARNT_TAU));
+                GTRY(lin(s1, x, 1.0, x, 1.0, p, SL_TAU, SL_HD));
+                GTRY(Ops<T>::dot2(g, w, rg, x, nullptr, nullptr, SL_D0, s1));
+                GTRY(ctlk(s1, G_ARNT_SLOPE));
+                GTRY(lin(s1, x, -1.0, rg, 0.0, nullptr, -1, SL_NEG));
+                GTRY(handle_in(1, &c_ls));
+                GTRY(ctlk(s1, G_ARNT_LS0, c_ls));
+                GTRY(while_node(1, c_ls, [&](cudaStream_t s2) -> int {
+                    GTRY(Ops<T>::retract(g, w, u, x, 1.0, o.retraction, z, s2, SL_T));
+                    GTRY(lin(s2, r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));
+                    GTRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s2));
+                    GTRY(Ops<T>::dot2(g, w, r, Hp, nullptr, nullptr, SL_MB, s2));
+                    return ctlk(s2, G_ARNT_LS, c_ls, 0, 3);
+                }));
+                GTRY(ctlk(s1, G_ARNT_E2));
+                GTRY(Ops<T>::energy(g, w, z, s1));
+                GTRY(ctlk(s1, G_ARNT_ACC));
+                GTRY(lin(s1, u, 1.0, z, 0.0, nullptr, -1, SL_ACC));
+                GTRY(Ops<T>::grad(g, w, u, gE, rg, true, s1));
+                return ctlk(s1, G_ARNT_END, c_arnt, 0, 4);
+            }));
+        }
+        // ---- the returned state: energy and gradient norm of every instance ----
+        GTRY(ctlk(s0, G_FINAL));
+        GTRY(Ops<T>::grad(g, w, u, nullptr, rg, true, s0));
+        if (cudaMemcpyAsync(Xdev, u, h->field_bytes, cudaMemcpyDeviceToDevice, s0) != cudaSuccess) return SBEC_ERR_CUDA;
+        return SBEC_OK;
+    }
+#undef GTRY
+};
+
+}  // namespace
+
+extern "C" int sbec_solve_graph(sbec_handle* const* handles, int nh, void* const* X, const sbec_solve_opts* opts,
+                                void* const* workspaces, const size_t* workspace_bytes, long long loop_cap,
+                                sbec_stats* const* stats) {
+    if (!handles || nh < 1 || nh > 16 || !X || !workspaces || !workspace_bytes || !stats) return SBEC_ERR_ARG;
+    sbec_solve_opts o;
+    if (opts) o = *opts; else sbec_solve_defaults(&o);
+    if (!opts_valid(o)) return SBEC_ERR_ARG;
+    if (loop_cap <= 0) loop_cap = 1000000;
+    sbec_handle* h0 = handles[0];
+    for (int i = 0; i < nh; ++i) {
+        sbec_handle* h = handles[i];
+        if (!h || !X[i] || !workspaces[i] || !stats[i]) return SBEC_ERR_ARG;
+        if (h->prob.precision != h0->prob.precision || h->device != h0->device || h->B > 1024) return SBEC_ERR_ARG;
+        if (workspace_bytes[i] < 10 * h->field_bytes || !sbec_is_device_ptr(workspaces[i]) ||
+            !sbec_is_device_ptr(X[i]))
+            return SBEC_ERR_ARG;
+        if (h->prof.enabled) return SBEC_ERR_ARG;     // event timing cannot be captured
+    }
+    const bool fp64 = h0->prob.precision == SBEC_FP64;
+    std::vector<void*> branches(nh, nullptr);
+    auto cleanup = [&]() {
+        for (int i = 0; i < nh; ++i) {
+            if (fp64) delete static_cast<GraphBranch<double>*>(branches[i]);
+            else delete static_cast<GraphBranch<float>*>(branches[i]);
+        }
+    };
+    for (int i = 0; i < nh; ++i) {
+        if (fp64) branches[i] = new GraphBranch<double>(handles[i], o, workspaces[i], X[i], loop_cap);
+        else branches[i] = new GraphBranch<float>(handles[i], o, workspaces[i], X[i], loop_cap);
+    }
+    // one capture: the origin stream forks into one stream per branch and joins them
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins(nh, nullptr);
+    int rc = SBEC_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        rc = SBEC_ERR_CUDA;
+    for (int i = 0; i < nh && !rc; ++i)
+        if (cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) != cudaSuccess) rc = SBEC_ERR_CUDA;
+    // the handles' streams finish their pending work before the graph starts
+    for (int i = 0; i < nh && !rc; ++i)
+        if (cudaStreamSynchronize(handles[i]->stream) != cudaSuccess) rc = SBEC_ERR_CUDA;
+    if (!rc && cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) rc = SBEC_ERR_CUDA;
+    bool capturing = !rc;
+    if (!rc && cudaEventRecord(fork, origin) != cudaSuccess) rc = SBEC_ERR_CUDA;
+    for (int i = 0; i < nh && !rc; ++i) {
+        cudaStream_t s0 = fp64 ? static_cast<GraphBranch<double>*>(branches[i])->st[0]
+                               : static_cast<GraphBranch<float>*>(branches[i])->st[0];
+        if (cudaStreamWaitEvent(s0, fork, 0) != cudaSuccess) { rc = SBEC_ERR_CUDA; break; }
+        rc = fp64 ? static_cast<GraphBranch<double>*>(branches[i])->build()
+                  : static_cast<GraphBranch<float>*>(branches[i])->build();
+        if (!rc && (cudaEventRecord(joins[i], s0) != cudaSuccess || cudaStreamWaitEvent(origin, joins[i], 0) != cudaSuccess))
+            rc = SBEC_ERR_CUDA;
+    }
+    if (capturing) {
+        const cudaError_t ce = cudaStreamEndCapture(origin, &graph);
+        if (!rc && ce != cudaSuccess) rc = SBEC_ERR_CUDA;
+    }
+    cudaGetLastError();
+    if (!rc && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = SBEC_ERR_CUDA;
+    if (!rc && (cudaGraphLaunch(exec, origin) != cudaSuccess || cudaStreamSynchronize(origin) != cudaSuccess))
+        rc = SBEC_ERR_CUDA;
+    // results: one read of every handle's scalar blocks
+    int out = rc;
+    for (int i = 0; i < nh && !rc; ++i) {
+        sbec_handle* h = handles[i];
+        if (sbec_read_scalars(h) == SBEC_ERR_CUDA) { out = SBEC_ERR_CUDA; break; }
+        const double tol = o.tol;
+        bool all = true;
+        for (int b = 0; b < h->B; ++b) {
+            const double* sc = h->h_scal + (size_t)b * sbec::S_COUNT;
+            sbec_stats& s = stats[i][b];
+            memset(&s, 0, sizeof(s));
+            s.energy = sc[SBEC_S_ENERGY];
+            s.grad_norm = sqrt(sc[SBEC_S_RGRAD_NORM2]);
+            s.outer_iters = (long long)sc[DS_OUTER];
+            s.inner_iters = (long long)sc[DS_INNER];
+            s.rgbb_iters = (long long)sc[DS_RGBBIT];
+            s.n_grad = (long long)sc[DS_NGRAD];
+            s.n_energy = (long long)sc[DS_NENERGY];
+            s.n_hvp = (long long)sc[DS_NHVP];
+            s.converged = s.grad_norm <= tol;
+            all = all && s.converged;
+            const int e = (int)sc[DS_ERR];
+            if (e && (out == SBEC_OK || out == SBEC_ERR_NOCONV)) out = e;
+        }
+        if (!all && out == SBEC_OK) out = SBEC_ERR_NOCONV;
+        if (clear_skip(h) && out == SBEC_OK) out = SBEC_ERR_CUDA;
+        h->last_grad_X = nullptr;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : joins)
+        if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (origin) cudaStreamDestroy(origin);
+    cleanup();
+    cudaGetLastError();
+    return out;
+}

@@ -539,6 +539,41 @@ def solve_cascadic_mixed(handles64, handles32, states, tol=1e-8, tol_coarse=1e-5
     return a, b
 
 
+_lib.sbec_solve_graph.argtypes = [ctypes.POINTER(_vp), _int, ctypes.POINTER(_vp), ctypes.POINTER(SolveOpts),
+                                  ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_size_t), ctypes.c_longlong,
+                                  ctypes.POINTER(ctypes.POINTER(Stats))]
+_lib.sbec_solve_graph.restype = _int
+
+
+def solve_graph(handles, Xs, tol=1e-8, method="arnt", retraction=1, maxit=10000, rgbb_tol=1e-2, rgbb_maxit=2000,
+                project=True, workspaces=None, loop_cap=0):
+    """sbec_solve_graph: the solves of every instance of the given handles as one CUDA
+    graph launch.  Xs[i] (device tensor of handle i) is overwritten.  Returns
+    (status, [list of per-instance stats dicts per handle]); raises SbecError on a
+    CUDA or argument error."""
+    o = _opts(method, retraction, tol, maxit, rgbb_tol, rgbb_maxit, project)
+    nh = len(handles)
+    sizes = []
+    for h in handles:
+        nb = ctypes.c_size_t()
+        _check(_lib.sbec_solve_workspace_bytes(h._h, ctypes.byref(nb)), "sbec_solve_workspace_bytes")
+        sizes.append(nb.value)
+    if workspaces is None:
+        import torch
+        workspaces = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+    stats = [(Stats * h.B)() for h in handles]
+    hs = (_vp * nh)(*[h._h for h in handles])
+    xs = (_vp * nh)(*[_ptr(x) for x in Xs])
+    ws = (_vp * nh)(*[_ptr(x) for x in workspaces])
+    nbs = (ctypes.c_size_t * nh)(*sizes)
+    sp = (ctypes.POINTER(Stats) * nh)(*[ctypes.cast(st, ctypes.POINTER(Stats)) for st in stats])
+    rc = _lib.sbec_solve_graph(hs, nh, xs, ctypes.byref(o), ws, nbs, int(loop_cap), sp)
+    if rc not in (OK, ERR_NOCONV, ERR_TIMEOUT):
+        _check(rc, "sbec_solve_graph")
+    return rc, [[{k: getattr(st[i], k) for k, _ in Stats._fields_} for i in range(h.B)]
+                for st, h in zip(stats, handles)]
+
+
 _lib.sbec_solve_batch.argtypes = [_vp, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.c_size_t, ctypes.POINTER(Stats)]
 _lib.sbec_solve_batch.restype = _int
 

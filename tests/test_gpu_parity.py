@@ -106,7 +106,15 @@ def test_fp64_retraction_parity(w, kind, dev):
             assert abs(got @ got - 1) < 1e-12 and abs(got @ (Gm * got) - w.M) < 1e-12
 
 
-@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[12]], ids=lambda w: w.name)
+# FP32 strided passes on TMA tiles: pass axes of 128 / 256 points, x a multiple of 16
+TMA_CASES = [
+    _wl(2, (32, 128, 128), 8.0, 0.3, (150.0, 4.0, -3.0, 0), lattice=6.0),     # 3D: y and z passes
+    _wl(3, (16, 256), 8.0, 0.9, (90.0, -1.0, 4.0, 1.5), lattice=4.0),        # 2D: fused y pass
+    _wl(1, (64, 32, 256), 8.0, 0.2, (60.0, 1.0, 0, 0)),                      # z on TMA, y (32) not
+]
+
+
+@pytest.mark.parametrize("w", [CASES[0], CASES[2], CASES[5], CASES[12]] + TMA_CASES, ids=lambda w: w.name)
 def test_mixed_precision_bound(w, dev):
     sbec = _sbec()
     P, u, Xf, Zf = case_inputs(w)
@@ -126,6 +134,33 @@ def test_mixed_precision_bound(w, dev):
     assert abs(E2 - E_ref) <= 2e-6 * abs(E_ref)
     assert rel(Ge.cpu().numpy(), O.to_fields(P, O.gradient(P, Xm))) <= 2e-5
     assert rel(H1.cpu().numpy(), O.to_fields(P, O.hessvec(P, Xm, Zm))) <= 2e-5
+
+
+@pytest.mark.parametrize("w", TMA_CASES, ids=lambda w: w.name)
+def test_mixed_riemannian_and_repeatable_on_tma_passes(w, dev):
+    # the Riemannian products through the TMA passes, and bitwise repeatability of
+    # the persistent tile loop (fixed tile order per block, fixed reduction order)
+    sbec = _sbec()
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf.astype(np.complex64)).to(dev)
+    Z = torch.from_numpy(Zf.astype(np.complex64)).to(dev)
+    Gr, H1, H2 = (torch.empty_like(X) for _ in range(3))
+    with sbec.Handle.from_workload(w, precision="mixed") as h:
+        E1 = h.energy(X)
+        E2, rn = h.grad(X, G_riem=Gr)
+        h.hessvec(X, Z, H1, sigma=0.2, riemannian=True)
+        h.hessvec(X, Z, H2, sigma=0.2, riemannian=True)
+        assert h.energy(X) == E1
+        h.sync()
+    assert torch.equal(H1, H2)
+    Xm = O.to_matrix(P, Xf.astype(np.complex64).astype(np.complex128))
+    Zm = O.to_matrix(P, Zf.astype(np.complex64).astype(np.complex128))
+    uu = O.to_u(P, Xm)
+    g = O.to_u(P, O.gradient(P, Xm))
+    rg = O.rgrad(P, uu, g)
+    assert abs(rn - np.linalg.norm(rg)) <= 2e-5 * np.linalg.norm(g)
+    Hr = O.rhess(P, uu, O.to_u(P, Zm), g=g, sigma=0.2)
+    assert rel(H1.cpu().numpy(), O.to_fields(P, O.from_u(P, Hr))) <= 2e-5
 
 
 def test_host_pointers_match_device(dev):
