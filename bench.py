@@ -67,13 +67,16 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm_gbs()
 PW_FLOPS = {"grad": {1: 170, 2: 375, 3: 760}, "hess": {1: 300, 2: 640, 3: 1400},
             "energy": {1: 70, 2: 140, 3: 290}}
 # DRAM traffic per launch from ncu captures of the unchanged kernels (bytes), by
-# (kernel, workload); profiles/ holds the summaries
+# (kernel, workload, form); profiles/ holds the summaries
 NCU_TRAFFIC = {
     # full capture of the 256^2 FP64 workload (the state stays in L2: one read per field)
-    ("s_k2", "spin2_2d_256x256"): 5328128.0,
+    ("s_k2", "spin2_2d_256x256", "fp64"): 5328128.0,
     # 128^3 capture of the same kernel (mean over its 8 launches, both forms) scaled by the
     # 8x larger fields (writes partly held in L2 at 128^3, so this is a lower bound at 256^3)
-    ("proj_apply", "spin3_3d_256cubed"): 8 * (234989280.0 + 81436448.0),
+    ("proj_apply", "spin3_3d_256cubed", "mixed"): 8 * (234989280.0 + 81436448.0),
+    # 128^3 capture of the FP64 spin-3 Hessian epilogue (reads 724.1 MB, writes 231.0 MB per
+    # launch) scaled by the 8x larger fields: 4 S + S_V, the algorithmic bytes
+    ("x_inv_hess", "spin3_3d_256cubed", "fp64"): 8 * (724088064.0 + 230976256.0),
 }
 
 
@@ -327,12 +330,12 @@ def roofline_of(prof, w, precision, B, wname, fp64_peak=None):
                "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz")
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
                 "frac": ach / peak if ach else None,
-                "traffic": NCU_TRAFFIC.get((kname, wname)), "kernel": kname, "kernel_share": kms / total,
+                "traffic": NCU_TRAFFIC.get((kname, wname, "fp64")), "kernel": kname, "kernel_share": kms / total,
                 "peak_source": src, "frac_of_nominal": ach / FP64_NOMINAL_GFLOPS if ach else None}
     by = bytes_model(w, kname, 8, B)
     ach = by / per_launch_s / 1e9 if by else None
     return {"bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": ach / HBM_PEAK_GBS if ach else None, "traffic": NCU_TRAFFIC.get((kname, wname)),
+            "frac": ach / HBM_PEAK_GBS if ach else None, "traffic": NCU_TRAFFIC.get((kname, wname, "mixed")),
             "kernel": kname, "kernel_share": kms / total, "peak_source": HBM_PEAK_SOURCE + " copy bandwidth (read + write bytes)"}
 
 

@@ -55,15 +55,18 @@ def _cascadic(make, n, dev, tol=1e-8, mixed=False, coarse=(4, 2), init=None):
     return st
 
 
-def _scalar_bound(make, n, dev, mixed=False):
+def _scalar_bound(make, n, dev, mixed=False, tol=1e-8):
     # the same problem with beta1 = beta2 = 0: its ground-state energy is the
-    # scalar-GPE one (the reduction pinned by the oracle's tests)
+    # scalar-GPE one (the reduction pinned by the oracle's tests).  Its minimisers
+    # form a continuum (every spinor direction with the constraints), so ARNT's
+    # last digits of ||grad|| come slowly; the energy, quadratic in the gradient,
+    # is settled long before
     from dataclasses import replace
 
     def scalar(m):
         w = make(m)
         return replace(w, beta=(w.beta[0], 0.0, 0.0, 0.0))
-    return _cascadic(scalar, n, dev, mixed=mixed, init=make)
+    return _cascadic(scalar, n, dev, mixed=mixed, init=make, tol=tol)
 
 
 @pytest.mark.parametrize("case", [1, 2, 3])
@@ -86,7 +89,7 @@ def test_spin2_3d_cyclic_reaches_the_scalar_bound(dev):
     printed = _printed("spin2_2d_3d_energies.txt")[(3, 3, 0.0)]
     make = lambda n: W.paper_spin2_3d_case(3, 0.0, n)
     st = _cascadic(make, 256, dev, mixed=True)
-    bound = _scalar_bound(make, 256, dev, mixed=True)
+    bound = _scalar_bound(make, 256, dev, mixed=True, tol=1e-6)
     assert st["converged"] and bound["converged"]
     assert abs(st["energy"] - bound["energy"]) <= 1e-9 * bound["energy"]
     assert st["energy"] < printed - 0.5
