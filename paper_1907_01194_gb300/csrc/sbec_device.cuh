@@ -37,6 +37,41 @@ template <typename T2> __device__ __forceinline__ void cfma(T2& a, T2 b, T2 c) {
     a.x += b.x * c.x - b.y * c.y; a.y += b.x * c.y + b.y * c.x;
 }
 
+// FP32 complex additions, subtractions and real scalings as paired-float instructions
+// (add/sub/mul/fma.rn.f32x2, sm_100 family): one instruction per complex value where the
+// scalar form takes two.  Each lane is rounded as the scalar instruction would round it,
+// so the results are the same bits.
+__device__ __forceinline__ unsigned long long f2_bits(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_of(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(r);
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(r);
+}
+template <> __device__ __forceinline__ float2 cscale<float2>(float2 a, float s) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(make_float2(s, s))));
+    return f2_of(r);
+}
+template <> __device__ __forceinline__ void caxpy<float2>(float2& a, float s, float2 b) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(b)), "l"(f2_bits(make_float2(s, s))), "l"(f2_bits(a)));
+    a = f2_of(r);
+}
+
 // ---------------------------------------------------------------------------
 // Per-thread running sums of the reductions.  FP64 form: a double.  Mixed form:
 // a float sum whose rounding error is carried in a second float (the error-free

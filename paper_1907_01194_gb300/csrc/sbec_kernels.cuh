@@ -258,6 +258,9 @@ struct XArgs {
     const double* scal;   // device scalar block: Lemma 4.2 alpha_g, beta_g (riemannian epilogue)
     int riem;
     int sigslot;          // >= 0: sigma is multiplied by the instance's scal[sigslot]
+    int zproj;            // Hessian of a Riemannian product: the direction read from `in` (x pass)
+                          // or Zd (epilogue) is Z, and the pass uses xi = P_u Z = Z - (a + b l) X
+                          // with a, b = the instance's scal[S_PA], scal[S_PB] (Lemma 4.1)
     double* partials;
     int nblk;
     PointParams pp;
@@ -696,6 +699,14 @@ __global__ void __launch_bounds__(512) k_xpass2(const XArgs a) {
         if (on) {
 #pragma unroll
             for (int j2 = 0; j2 < N2; ++j2) v[j2] = row[q + N1 * j2];
+            if (MODE == X_FWD && a.zproj) {
+                // xi = Z - (a + b l) X on the fly: the projected direction is never stored
+                const double* sc = a.scal + inst * S_COUNT;
+                const T cf = T(sc[S_PA] + sc[S_PB] * double(F - cc));
+                const T2* __restrict__ xrow = reinterpret_cast<const T2*>(a.X) + roff;
+#pragma unroll
+                for (int j2 = 0; j2 < N2; ++j2) caxpy(v[j2], -cf, xrow[q + N1 * j2]);
+            }
             level_a_fwd<T2, LOGN, false>(v, q, tw);
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) my[k2 * (N1 + 1) + q] = v[k2];
@@ -770,15 +781,19 @@ __host__ __device__ constexpr size_t epi_stage_bytes() {
            (size_t)kEpiThreads * sizeof(T);
 }
 // Resident blocks per SM the epilogue is compiled for: two in FP32 (its pointwise
-// algebra fits 128 registers), one in FP64 (the FP64 pipe, not latency, bounds it)
-template <typename T> struct EpiBlocks { static constexpr int v = sizeof(T) == 4 ? 2 : 1; };
+// algebra fits 128 registers), except the spin-3 Hessian, whose algebra spills at 128
+// registers and runs faster as one block with three copy stages; one in FP64 (the
+// FP64 pipe, not latency, bounds it)
+template <typename T, int F, bool HESS> struct EpiBlocks {
+    static constexpr int v = (sizeof(T) == 4 && !(HESS && F >= 3)) ? 2 : 1;
+};
 
 // copies in flight: points k + 1 and k + 2 while point k is computed, when three
 // stages of every resident block fit in 200 KB of shared memory, else point k + 1 only
 template <typename T, int F, bool HESS>
 __host__ __device__ constexpr int epi_stages() {
-    return 3 * EpiBlocks<T>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024   ? 3
-           : 2 * EpiBlocks<T>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024 ? 2
+    return 3 * EpiBlocks<T, F, HESS>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024   ? 3
+           : 2 * EpiBlocks<T, F, HESS>::v * epi_stage_bytes<T, F, HESS>() <= 200 * 1024 ? 2
                                                                               : 1;
 }
 template <typename T, int F, bool HESS>
@@ -787,7 +802,7 @@ __host__ __device__ constexpr size_t epi_smem() {
 }
 
 template <typename T, int F, bool HESS>
-__global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T>::v) k_epilogue(const XArgs a, const void* lxp, long long G) {
+__global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilogue(const XArgs a, const void* lxp, long long G) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
     constexpr int NQ = HESS ? 2 * C : 1 + 2 * C;
@@ -808,8 +823,13 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T>::v) k_epilogue(const
     T2* stg = reinterpret_cast<T2*>(smem_raw);                       // [NS][NA C][P]
     T* vst = reinterpret_cast<T*>(stg + NS * NA * C * P);            // [NS][P]
     const int tid = threadIdx.x;
-    T shift[C];
+    T shift[C], zcf[C];
     if (HESS) hess_shift<F, T>(a, scal, shift);
+    if (HESS && a.zproj) {
+        // Lemma 4.1 coefficients of Z, read before this launch's own finalize rewrites them
+#pragma unroll
+        for (int c = 0; c < C; ++c) zcf[c] = T(scal[S_PA] + scal[S_PB] * double(F - c));
+    }
     Acc<T> acc[NQ];
     const long long stride = (long long)gridDim.x * P;
     // copies of point p into stage st (none past the end; the group is committed anyway)
@@ -856,6 +876,10 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T>::v) k_epilogue(const
             T2 z[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) z[c] = sx[(2 * C + c) * P];
+            if (a.zproj) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) caxpy(z[c], -zcf[c], x[c]);
+            }
             hess_point<F, T2>(x, z, D, V, pp, l, o);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -1779,7 +1803,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     XArgs a;
     a.in = in; a.out = out; a.X = nullptr; a.Zd = nullptr; a.V = g.V; a.tw = g.tw[0];
     a.lam2x = g.lam2[0]; a.k2x = g.k2s[0]; a.G = g.G; a.logn = g.logn[0]; a.rpb = c.rpb; a.invG = g.invG;
-    a.sigma = 0.0; a.scal = nullptr; a.riem = 0; a.sigslot = -1;
+    a.sigma = 0.0; a.scal = nullptr; a.riem = 0; a.sigslot = -1; a.zproj = 0;
     a.partials = part; a.nblk = c.nblk;
     a.pp = point_params(g);
     a.rpi = g.G / g.n[0];
@@ -1899,15 +1923,20 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
     const void* zin = Z;
     // P_u coefficients (Lemma 4.1) into S_PA, S_PB by the last block per instance
     const FinProj fpz = fin_proj(g, w, -1, 0, C, S_PA, S_PB, 0);
+    const XCfg c = xcfg<T>(g);
+    // 2D/3D with the two-level x pass: xi = P_u Z is formed where Z is read (the x pass
+    // and the epilogue), so it is never stored; otherwise it is stored first
+    const bool fuse = riem && g.dim > 1 && c.two;
     if (riem) {
-        // xi = P_u Z (Lemma 4.1)
+        // the Lemma 4.1 coefficients of Z
         const int nd = SBEC_ELEM_GRID(g.G, (k_dot_reduce<T, F>));
         SBEC_LAUNCH(K_DOT, (k_dot_reduce<T, F>), dim3(nd, g.nl), 256, X, Z, g.G, w.partB, w.scal, g.imap, fpz);
-        SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F, false>), dim3(nb, g.nl), 256, X, Z, w.work2, g.G, w.scal, S_PA,
-                    S_PB, nullptr, g.imap, -1);
-        zin = w.work2;
+        if (!fuse) {
+            SBEC_LAUNCH(K_PROJ, (k_proj_apply<T, F, false>), dim3(nb, g.nl), 256, X, Z, w.work2, g.G, w.scal, S_PA,
+                        S_PB, nullptr, g.imap, -1);
+            zin = w.work2;
+        }
     }
-    const XCfg c = xcfg<T>(g);
     // the Lemma 4.2 coefficients alpha_g, beta_g are read by the epilogue from the
     // scalar block written by the latest gradient at X
     int st;
@@ -1918,12 +1947,15 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         st = launch_x<T, F, X_FULL_HESS>(c, a, w, s);
         if (st) return st;
     } else {
-        st = launch_x<T, F, X_FWD>(c, xargs<T>(g, c, zin, w.work, nullptr), w, s);
+        XArgs ax = xargs<T>(g, c, zin, w.work, nullptr);
+        if (fuse) { ax.X = X; ax.scal = w.scal; ax.zproj = 1; }
+        st = launch_x<T, F, X_FWD>(c, ax, w, s);
         if (st) return st;
         st = middle_passes<T>(g, w, s);
         if (st) return st;
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
+        a.zproj = fuse ? 1 : 0;
         if (riem) a.fp = fpz;
         // inverse x-FFT in place, then the Hessian epilogue (split as in grad_F)
         st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
