@@ -127,6 +127,15 @@ struct Lin {
     int guard;
 };
 
+// Scalar-block slots of the modified CG (the solver's layout), for the fused CG kernels:
+// kap, kap + 1 = <p,Hp>, <p,p>; alpha, alpha + 1 = the step and its guard; rr_now /
+// rr_next = <r,r> before / after the update; beta, j, stop, maxin, cg, sest, cgneg, cghd
+// as the solver documents them; skip_val = the S_SKIP value of an instance whose CG ended.
+struct CgSlots {
+    int kap, alpha, rr_now, rr_next, beta, j, stop, maxin, cg, sest, cgneg, cghd;
+    double skip_val;
+};
+
 // per-precision entry points (implemented in sbec_kernels_f64.cu / _f32.cu)
 template <typename T> struct Ops {
     static int lincomb(const Geom& g, const Work& w, const Lin& L, int dot_slot, cudaStream_t s);
@@ -136,6 +145,13 @@ template <typename T> struct Ops {
                       int slot, cudaStream_t s);
     static int ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp,
                      double eps, cudaStream_t s, int mask = -1);
+    // one modified-CG iteration after Hp = Hess p: cg_curv stores <p,Hp>, <p,p> and the
+    // guarded step alpha = <r,r> / <p,Hp>; cg_update applies x += alpha p, r -= alpha Hp,
+    // stores <r,r> and runs the CG control (iteration count, stopping tests, beta)
+    static int cg_curv(const Geom& g, const Work& w, const void* p, const void* Hp, const CgSlots& cs,
+                       cudaStream_t s);
+    static int cg_update(const Geom& g, const Work& w, void* x, void* r, const void* p, const void* Hp,
+                         const CgSlots& cs, cudaStream_t s);
     static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
     static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
                     cudaStream_t s);

@@ -1289,6 +1289,107 @@ static __global__ void k_fin_sums(const double* pa, int na_tot, int na_inst, int
     }
 }
 
+// Modified-CG iteration, fused (Sec. 5, Eq. prob-lsub, the CG of the ARNT subproblem).
+// k_cg_curv: partials <p, Hp>, <p, p>; the last block per instance stores them and the
+// guarded step alpha = <r,r> / <p,Hp> (alpha = 0 and guard 0 when <p,Hp> <= 1e-12 <p,p>).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_curv(const void* Pp, const void* Hpp, long long N, double* partials,
+                                                 double* scal0, const int* imap, const CgSlots cs) {
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long off = inst * N;
+    const T* __restrict__ P = reinterpret_cast<const T*>(Pp) + off;
+    const T* __restrict__ H = reinterpret_cast<const T*>(Hpp) + off;
+    Acc<T> acc[2];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const T pi = P[i];
+        acc[0].add(pi * H[i]);
+        acc[1].add(pi * pi);
+    }
+    double v[2];
+    acc_values(acc, v);
+    const int ntot = gridDim.x * gridDim.y;
+    block_reduce_store<2>(v, partials, ntot, blockIdx.y * gridDim.x + blockIdx.x);
+    double* scal = scal0 + (size_t)inst * S_COUNT;
+    if (!last_block(scal, gridDim.x)) return;
+    __shared__ double sums[2];
+    const int qs[2] = {0, 1};
+    warp_sums(partials, ntot, blockIdx.y * gridDim.x, gridDim.x, qs, 2, sums);
+    if (threadIdx.x == 0) {
+        const double kap = sums[0], pp = sums[1];
+        scal[cs.kap] = kap;
+        scal[cs.kap + 1] = pp;
+        if (!isfinite(kap) || !isfinite(pp)) set_status(scal, SBEC_ERR_NONFINITE);
+        const bool ok = kap > 1e-12 * pp;
+        scal[cs.alpha] = ok ? scal[cs.rr_now] / kap : 0.0;
+        scal[cs.alpha + 1] = ok ? 1.0 : 0.0;
+    }
+}
+
+// k_cg_update: x += alpha p and r -= alpha Hp (when the step's guard holds), partials
+// <r,r>; the last block per instance stores <r,r> and takes the CG's decision: count
+// the iteration; end the CG on curvature <p,Hp> <= 1e-12 <p,p> (recording sigma_est =
+// |<p,Hp>| / <p,p> and which direction Eq. (xi) takes), on ||r|| <= the threshold or at
+// the iteration cap; otherwise beta = <r',r'> / <r,r>.  An instance whose CG ends is
+// switched off (S_SKIP), so the rest of its chunk leaves it alone.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(void* Xp, void* Rp, const void* Pp, const void* Hpp, long long N,
+                                                   double* partials, double* scal0, const int* imap,
+                                                   const CgSlots cs) {
+    const long long inst = inst_of(imap, blockIdx.y);
+    if (skipped(scal0, inst)) return;
+    const long long off = inst * N;
+    double* scal = scal0 + (size_t)inst * S_COUNT;
+    T* __restrict__ X = reinterpret_cast<T*>(Xp) + off;
+    T* __restrict__ R = reinterpret_cast<T*>(Rp) + off;
+    const T* __restrict__ P = reinterpret_cast<const T*>(Pp) + off;
+    const T* __restrict__ H = reinterpret_cast<const T*>(Hpp) + off;
+    const bool upd = scal[cs.alpha + 1] != 0.0;
+    const T a = T(scal[cs.alpha]), na = T(-scal[cs.alpha]);
+    Acc<T> acc[1];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        T ri = R[i];
+        if (upd) {
+            X[i] = fma(a, P[i], X[i]);
+            ri = fma(na, H[i], ri);
+            R[i] = ri;
+        }
+        acc[0].add(ri * ri);
+    }
+    double v[1];
+    acc_values(acc, v);
+    const int ntot = gridDim.x * gridDim.y;
+    block_reduce_store<1>(v, partials, ntot, blockIdx.y * gridDim.x + blockIdx.x);
+    if (!last_block(scal, gridDim.x)) return;
+    __shared__ double sums[1];
+    const int qs[1] = {0};
+    warp_sums(partials, ntot, blockIdx.y * gridDim.x, gridDim.x, qs, 1, sums);
+    if (threadIdx.x == 0) {
+        const double rrn = sums[0];
+        scal[cs.rr_next] = rrn;
+        if (!isfinite(rrn)) set_status(scal, SBEC_ERR_NONFINITE);
+        const double kap = scal[cs.kap], pp = scal[cs.kap + 1];
+        const double j = scal[cs.j] + 1.0;
+        scal[cs.j] = j;
+        bool done;
+        if (kap <= 1e-12 * pp) {
+            scal[cs.sest] = fabs(kap) / pp;
+            if (j == 1.0) scal[cs.cgneg] = 1.0;
+            else if (kap < -1e-12 * pp) scal[cs.cghd] = 1.0;
+            done = true;
+        } else if (sqrt(rrn) <= scal[cs.stop]) {
+            done = true;
+        } else {
+            scal[cs.beta] = rrn / scal[cs.rr_now];
+            done = j >= scal[cs.maxin];
+        }
+        if (done) {
+            scal[cs.cg] = 0.0;
+            scal[S_SKIP] = cs.skip_val;
+        }
+    }
+}
+
 // scal[dst] = scal[num] / scal[den] when the guard holds, else 0  (CG alpha), per
 // instance; scal[dst + 1] is the guard flag of the guarded updates
 static __global__ void k_ratio(double* scal0, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
@@ -2057,6 +2158,23 @@ template <typename T>
 int Ops<T>::ratio(const Geom& g, const Work& w, int dst, int num, int den, int guard_kap, int guard_pp, double eps,
                   cudaStream_t s, int mask) {
     SBEC_LAUNCH(K_FIN, k_ratio, g.nl, 32, w.scal, dst, num, den, guard_kap, guard_pp, eps, mask, g.imap);
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::cg_curv(const Geom& g, const Work& w, const void* p, const void* Hp, const CgSlots& cs, cudaStream_t s) {
+    const long long N = 2LL * g.C * g.G;
+    const int nb = SBEC_ELEM_GRID(N / 2, k_cg_curv<T>);
+    SBEC_LAUNCH(K_DOT, k_cg_curv<T>, dim3(nb, g.nl), 256, p, Hp, N, w.partB, w.scal, g.imap, cs);
+    return SBEC_OK;
+}
+
+template <typename T>
+int Ops<T>::cg_update(const Geom& g, const Work& w, void* x, void* r, const void* p, const void* Hp,
+                      const CgSlots& cs, cudaStream_t s) {
+    const long long N = 2LL * g.C * g.G;
+    const int nb = SBEC_ELEM_GRID(N / 2, k_cg_update<T>);
+    SBEC_LAUNCH(K_LIN, k_cg_update<T>, dim3(nb, g.nl), 256, x, r, p, Hp, N, w.partB, w.scal, g.imap, cs);
     return SBEC_OK;
 }
 

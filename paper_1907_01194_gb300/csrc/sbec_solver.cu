@@ -3,7 +3,7 @@
 // and ARNT (regularised Newton model m_k, modified CG, curvilinear Armijo
 // search, ratio test and sigma update).  Every vector operation runs on the
 // device.  The modified CG runs in chunks of cg_chunk iterations whose
-// coefficients and stopping tests are computed on the device (k_cg_ctl), each
+// coefficients and stopping tests are computed on the device (k_cg_update), each
 // chunk the replay of a CUDA graph (one per state array, slot parity and set of
 // launched instances); the host reads the scalar block once per
 // chunk, line-search trial or outer iteration and keeps the rest of the control
@@ -71,38 +71,6 @@ static_assert(int(SL_CGHD) < int(sbec::S_COUNT), "solver slots exceed the scalar
 // S_SKIP value of an instance whose modified CG has ended inside a chunk
 constexpr double kSkipCg = 2.0;
 
-// Modified-CG bookkeeping of one iteration, one thread per instance (after the
-// x and r updates): counts the iteration; ends the CG on non-positive curvature
-// <p,Hp> <= 1e-12 <p,p> (recording sigma_est and which direction Eq. (xi)
-// takes), on ||r|| <= the threshold or at the iteration cap; otherwise writes
-// beta = <r',r'>/<r,r> for the update p = r' + beta p.  An instance that ends
-// sets S_SKIP so that the rest of its chunk leaves its arrays and scalars alone.
-__global__ void k_cg_ctl(double* scal0, int nl, const int* imap, int rr_now, int rr_next) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nl) return;
-    double* sc = scal0 + (size_t)(imap ? imap[b] : b) * sbec::S_COUNT;
-    if (sc[sbec::S_SKIP] != 0.0) return;
-    const double kap = sc[SL_KAP], pp = sc[SL_KAP + 1], rrn = sc[rr_next];
-    const double j = sc[SL_J] + 1.0;
-    sc[SL_J] = j;
-    bool done;
-    if (kap <= 1e-12 * pp) {
-        sc[SL_SEST] = fabs(kap) / pp;
-        if (j == 1.0) sc[SL_CGNEG] = 1.0;
-        else if (kap < -1e-12 * pp) sc[SL_CGHD] = 1.0;
-        done = true;
-    } else if (sqrt(rrn) <= sc[SL_STOP]) {
-        done = true;
-    } else {
-        sc[SL_BETA] = rrn / sc[rr_now];
-        done = j >= sc[SL_MAXIN];
-    }
-    if (done) {
-        sc[SL_CG] = 0.0;
-        sc[sbec::S_SKIP] = kSkipCg;
-    }
-}
-
 // elementwise precision change of n reals
 template <typename TS, typename TD>
 __global__ void k_cast(const TS* __restrict__ src, TD* __restrict__ dst, long long n) {
@@ -133,7 +101,7 @@ int clear_skip(sbec_handle* h) {
 // Chunks of the modified CG (Sec. 5, Eq. prob-lsub) on Hess m_k p = Hess f p +
 // sigma p with sigma from each instance's SL_SIG: per iteration the projected
 // Hessian-vector product, <p,Hp> and <p,p>, alpha = <r,r>/<p,Hp> (guarded),
-// x += alpha p, r -= alpha Hp with <r,r>, k_cg_ctl and p = r + beta p.  With
+// x += alpha p, r -= alpha Hp with <r,r> and the CG control, p = r + beta p.  With
 // graphs, the chunk for a given state array and slot parity is captured once
 // on a private stream and replayed on the handle's stream.
 template <typename T>
@@ -162,22 +130,18 @@ struct CgChunks {
         return Ops<T>::lincomb(g, w, L, slot, cs);
     }
 
+    // one iteration: Hp = Hess p; <p,Hp>, <p,p> and alpha (k_cg_curv); x, r, <r,r> and
+    // the CG control (k_cg_update, in its last block per instance); p = r + beta p
     int launch(cudaStream_t cs, const void* u, void* p, void* Hp, void* x, void* r, int par0) {
         for (int i = 0; i < K; ++i) {
             const int par = (par0 + i) & 1;
             const int rr_now = par ? SL_RRB : SL_RRA, rr_next = par ? SL_RRA : SL_RRB;
+            const sbec::CgSlots sl{SL_KAP, SL_ALPHA, rr_now, rr_next, SL_BETA, SL_J, SL_STOP, SL_MAXIN,
+                                   SL_CG, SL_SEST, SL_CGNEG, SL_CGHD, kSkipCg};
             int e = Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, cs, SL_SIG);
-            if (!e) e = Ops<T>::dot2(g, w, p, Hp, p, p, SL_KAP, cs);
-            if (!e) e = Ops<T>::ratio(g, w, SL_ALPHA, rr_now, SL_KAP, SL_KAP, SL_KAP + 1, 1e-12, cs);
-            if (!e) e = lin(cs, x, x, 1.0, p, SL_ALPHA, SL_ALPHA + 1, nullptr, SL_D0);
-            if (!e) e = lin(cs, r, r, -1.0, Hp, SL_ALPHA, SL_ALPHA + 1, r, rr_next);
-            if (e) return e;
-            {
-                sbec::ProfScope ps(w.prof, sbec::K_FIN, cs);
-                k_cg_ctl<<<(g.nl + 127) / 128, 128, 0, cs>>>(w.scal, g.nl, g.imap, rr_now, rr_next);
-                if (cudaGetLastError() != cudaSuccess) return SBEC_ERR_CUDA;
-            }
-            e = lin(cs, p, r, 1.0, p, SL_BETA, -1, nullptr, SL_D0);
+            if (!e) e = Ops<T>::cg_curv(g, w, p, Hp, sl, cs);
+            if (!e) e = Ops<T>::cg_update(g, w, x, r, p, Hp, sl, cs);
+            if (!e) e = lin(cs, p, r, 1.0, p, SL_BETA, -1, nullptr, SL_D0);
             if (e) return e;
         }
         return SBEC_OK;
@@ -395,7 +359,7 @@ struct Solver {
                 ds = sbec_read_scalars(h32);
                 if (ds) return ds;
                 if (q[SL_CG] == 0.0) break;
-                if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+                if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_update ends every CG by the cap
             }
             const long long its = (long long)q[SL_J];
             st->inner_iters += its;
@@ -451,7 +415,7 @@ struct Solver {
                 rr = sc(SL_RRA);
             }
             if (!in && rr > 0.0) {
-                // device-driven chunks (k_cg_ctl); the host reads the block once per chunk
+                // device-driven chunks (k_cg_update); the host reads the block once per chunk
                 double* hsc = h->h_scal;
                 hsc[SL_SIG] = sigma; hsc[SL_STOP] = stop; hsc[SL_MAXIN] = (double)max_inner;
                 hsc[SL_J] = 0.0; hsc[SL_CG] = 1.0; hsc[SL_SEST] = -1.0; hsc[SL_CGNEG] = 0.0; hsc[SL_CGHD] = 0.0;
@@ -463,7 +427,7 @@ struct Solver {
                     done_its += cgc.K;
                     PULL(ds);
                     if (sc(SL_CG) == 0.0) break;
-                            if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+                            if (done_its >= max_inner) return SBEC_ERR_CUDA;   // k_cg_update ends every CG by the cap
                 }
                 const long long its = (long long)sc(SL_J);
                 st->inner_iters += its;
@@ -782,7 +746,7 @@ struct BatchSolver {
             if (incg) {
                 runset(cg);                              // instances outside the CG keep p, Hp, x, r
                 TRY(push());
-                // device-driven chunks (k_cg_ctl); the host reads the blocks once per chunk
+                // device-driven chunks (k_cg_update); the host reads the blocks once per chunk
                 long long done_its = 0;
                 while (true) {
                     TRY(cgc.run(u, p, Hp, x, r, (int)(done_its & 1)));
@@ -791,7 +755,7 @@ struct BatchSolver {
                     int still = 0;
                     for (int b = 0; b < B; ++b) still += (cg[b] && hs(b)[SL_CG] != 0.0) ? 1 : 0;
                     if (!still) break;
-                    if (done_its >= cap_in) return SBEC_ERR_CUDA;   // k_cg_ctl ends every CG by the cap
+                    if (done_its >= cap_in) return SBEC_ERR_CUDA;   // k_cg_update ends every CG by the cap
                     // once half of the launched instances have ended their CG, narrow the
                     // launches to the others (a new chunk graph per launched set)
                     if (2 * still <= h->geom.nl) TRY(push());
