@@ -66,6 +66,11 @@ HBM_PEAK_GBS, HBM_PEAK_SOURCE = _measured_hbm_gbs()
 # ladder / pair form the kernels use: densities, then each output component's terms)
 PW_FLOPS = {"grad": {1: 170, 2: 375, 3: 760}, "hess": {1: 300, 2: 640, 3: 1400},
             "energy": {1: 70, 2: 140, 3: 290}}
+# the share of those counts that forms the densities (rho, F_z, F_+, A00, A_{2l}): the
+# energy count less its energy-density terms.  The FP64 Hessian epilogue of a 2D / 3D
+# product at the state of the latest gradient (every product of the bench's step and of
+# the solvers) reads the densities that gradient stored instead of forming them
+DENS_FLOPS = {1: 45, 2: 100, 3: 225}
 # DRAM traffic per launch from ncu captures of the unchanged kernels (bytes), by
 # (kernel, workload, form); profiles/ holds the summaries
 NCU_TRAFFIC = {
@@ -74,9 +79,6 @@ NCU_TRAFFIC = {
     # 128^3 capture of the same kernel (mean over its 8 launches, both forms) scaled by the
     # 8x larger fields (writes partly held in L2 at 128^3, so this is a lower bound at 256^3)
     ("proj_apply", "spin3_3d_256cubed", "mixed"): 8 * (234989280.0 + 81436448.0),
-    # 128^3 capture of the FP64 spin-3 Hessian epilogue (reads 724.1 MB, writes 231.0 MB per
-    # launch) scaled by the 8x larger fields: 4 S + S_V, the algorithmic bytes
-    ("x_inv_hess", "spin3_3d_256cubed", "fp64"): 8 * (724088064.0 + 230976256.0),
 }
 
 
@@ -295,7 +297,7 @@ def flops_model(w, kname, B=1):
     if kname == "x_inv_grad":
         return B * G * PW_FLOPS["grad"][w.F]
     if kname == "x_inv_hess":
-        return B * G * PW_FLOPS["hess"][w.F]
+        return B * G * (PW_FLOPS["hess"][w.F] - DENS_FLOPS[w.F])
     if kname == "x_full_grad":
         return B * (C * (2 * fft(n[0]) + 4 * n[0]) + G * PW_FLOPS["grad"][w.F])
     if kname == "x_full_hess":

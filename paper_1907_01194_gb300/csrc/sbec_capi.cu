@@ -127,6 +127,7 @@ void free_handle(sbec_handle* h) {
     cudaFree(h->work.partA);
     cudaFree(h->work.partB);
     cudaFree(h->work.scal);
+    cudaFree(h->work.dens);
     cudaFree(h->d_ppb);
     cudaFree(h->d_Mb);
     cudaFree(h->d_imap);
@@ -248,6 +249,9 @@ int create_impl(const sbec_problem* probs, int B, const double* V, void* cuda_st
     ok = ok && cudaMalloc((void**)&h->work.partA, part * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->work.partB, part * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->work.scal, nscal * sizeof(double)) == cudaSuccess;
+    if (dbl && g.dim >= 2)
+        ok = ok && cudaMalloc((void**)&h->work.dens, (size_t)B * sbec::dens_count(g.F) * g.G * sizeof(double)) ==
+                       cudaSuccess;
     for (int i = 0; i < 3; ++i) ok = ok && cudaMalloc(&h->stage[i], h->field_bytes) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&h->h_scal, nscal * sizeof(double)) == cudaSuccess;
     if (ok && B > 1) {
@@ -472,8 +476,10 @@ int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int
         if (st) return st;
         h->last_grad_X = X;
     }
-    st = dbl ? sbec::Ops<double>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream)
-             : sbec::Ops<float>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream);
+    // the densities stored by the latest gradient are those of X when it was at X
+    const bool dens = h->last_grad_X == X;
+    st = dbl ? sbec::Ops<double>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream, -1, dens)
+             : sbec::Ops<float>::hessvec(h->geom, h->work, Xd, Zd, sigma, riemannian, hz, h->stream, -1, dens);
     if (st) return st;
     if ((st = copy_back(h, HZ, hz))) return st;
     if (host) st = read_scalars(h);

@@ -13,6 +13,10 @@ namespace sbec {
 // Spins the kernels are instantiated for: F = 1..kMaxF (C = 2F + 1 components)
 constexpr int kMaxF = 4;
 constexpr int kMaxC = 2 * kMaxF + 1;
+// Real values per grid point of the densities a Hessian epilogue reads (Sec. 2):
+// rho, F_z, F_+ (2), and for F = 2, 4 the singlet amplitude A00 (2), for F = 3
+// A00 and the five quintet amplitudes A_{2l} (2 each)
+__host__ __device__ constexpr int dens_count(int F) { return F == 1 ? 4 : F == 3 ? 16 : 6; }
 
 // device scalar-block slots beyond the public SBEC_S_* ones
 enum {
@@ -108,6 +112,10 @@ struct Work {
     double* partB;
     size_t part_cap;   // doubles in each of partA / partB
     double* scal;      // device scalar block (S_COUNT doubles)
+    // FP64 handles in 2D and 3D: the densities of the latest gradient, dens_count(F)
+    // planes of G doubles per instance ([B][q][G]), written by the gradient epilogue
+    // and read by the Hessian epilogues at the same state; null otherwise
+    double* dens;
     int num_sms;
     Prof* prof;
 };
@@ -155,9 +163,11 @@ template <typename T> struct Ops {
     static int energy(const Geom& g, const Work& w, const void* X, cudaStream_t s);
     static int grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* Griem, bool want_norm,
                     cudaStream_t s);
-    // sigslot / tslot >= 0: sigma / t multiplied by each instance's scalar-block slot
+    // sigslot / tslot >= 0: sigma / t multiplied by each instance's scalar-block slot;
+    // dens: the latest grad on w was at X (X unchanged since), so the Hessian epilogue
+    // may read the densities it stored in w.dens instead of forming them again
     static int hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem,
-                       void* HZ, cudaStream_t s, int sigslot = -1);
+                       void* HZ, cudaStream_t s, int sigslot = -1, bool dens = false);
     static int retract(const Geom& g, const Work& w, const void* U, const void* Xi, double t, int kind,
                        void* out, cudaStream_t s, int tslot = -1);
     static int prolongate(const Geom& gc, const Work& wc, const void* Xc, const Geom& gf, const Work& wf,

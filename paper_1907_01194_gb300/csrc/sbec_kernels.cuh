@@ -271,6 +271,9 @@ struct XArgs {
     FinProj fp;                 // fp.on: Lemma 4.1 finalize by the last block per instance
     int fe;                     // X_FULL_ENERGY: energy finalize by the last block per
                                 // instance, into the scalar blocks fp.scal0
+    double* dens;               // FP64 stand-alone epilogues: densities per point, stored by
+                                // the gradient epilogue and read by the Hessian epilogue
+                                // ([B][dens_count(F)][G]), or null
 };
 
 // Shift of the Hessian epilogue per component: sigma (times the instance's
@@ -801,7 +804,31 @@ __host__ __device__ constexpr size_t epi_smem() {
     return epi_stages<T, F, HESS>() * epi_stage_bytes<T, F, HESS>();
 }
 
-template <typename T, int F, bool HESS>
+// The densities of a point in dens_count(F) planes of G doubles: rho, F_z, F_+, then
+// A00 (F >= 2) and the quintet amplitudes A_{2l} (F = 3)
+template <int F>
+__device__ __forceinline__ void dens_store(const Dens<F, double2>& D, double* __restrict__ d, long long G) {
+    d[0] = D.rho; d[G] = D.Fz; d[2 * G] = D.Fp.x; d[3 * G] = D.Fp.y;
+    if (F >= 2) { d[4 * G] = D.A00.x; d[5 * G] = D.A00.y; }
+    if (F == 3) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) { d[(6 + 2 * k) * G] = D.A2[k].x; d[(7 + 2 * k) * G] = D.A2[k].y; }
+    }
+}
+template <int F>
+__device__ __forceinline__ void dens_load(Dens<F, double2>& D, const double* __restrict__ d, long long G) {
+    D.rho = __ldg(d); D.Fz = __ldg(d + G); D.Fp = make_double2(__ldg(d + 2 * G), __ldg(d + 3 * G));
+    D.A00 = make_double2(0.0, 0.0);
+    if (F >= 2) D.A00 = make_double2(__ldg(d + 4 * G), __ldg(d + 5 * G));
+    if (F == 3) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) D.A2[k] = make_double2(__ldg(d + (6 + 2 * k) * G), __ldg(d + (7 + 2 * k) * G));
+    }
+}
+
+// DC: 0 densities formed from X; 1 (FP64 gradient) formed and stored to a.dens;
+// 2 (FP64 Hessian) read from a.dens, stored there by the gradient at the same X
+template <typename T, int F, bool HESS, int DC>
 __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilogue(const XArgs a, const void* lxp, long long G) {
     using T2 = typename C2<T>::t;
     constexpr int C = 2 * F + 1;
@@ -818,6 +845,8 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilo
     const T* __restrict__ Vp = reinterpret_cast<const T*>(a.V) + inst * G;
     const PPT<T> pp(a.ppb ? a.ppb[inst] : a.pp);
     const double* scal = a.scal ? a.scal + inst * S_COUNT : nullptr;
+    static_assert(DC == 0 || (sizeof(T) == 8 && (DC == 1) == !HESS), "density cache: FP64 gradient / Hessian");
+    double* __restrict__ dens = DC ? a.dens + inst * (long long)dens_count(F) * G : nullptr;
     if (skipped(a.skip, inst)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* stg = reinterpret_cast<T2*>(smem_raw);                       // [NS][NA C][P]
@@ -851,6 +880,8 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilo
     for (int k = 0; k < NS - 1; ++k) issue(pt + k * stride, k);
     for (int k = 0; pt < G; ++k, pt += stride) {
         issue(pt + (NS - 1) * stride, (k + NS - 1) % NS);
+        Dens<F, T2> D;
+        if constexpr (DC == 2) dens_load<F>(D, dens + pt, G);    // in flight during the wait
         cp_async_wait<NS - 1>();                     // this thread's copies of point pt are in
         const int sk = k % NS;
         const T2* sx = stg + (size_t)sk * NA * C * P + tid;
@@ -858,8 +889,8 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilo
 #pragma unroll
         for (int c = 0; c < C; ++c) { x[c] = sx[c * P]; l[c] = sx[(C + c) * P]; }
         const T V = vst[sk * P + tid];
-        Dens<F, T2> D;
-        D.compute(x);
+        if constexpr (DC != 2) D.compute(x);
+        if constexpr (DC == 1) dens_store<F>(D, dens + pt, G);
         if (!HESS) {
             grad_point<F, T2>(x, D, V, pp, l, o);
             T ek = 0;
@@ -1868,9 +1899,9 @@ static int launch_pass(const Geom& g, const SCfg& c, const SArgs& a, const Work&
         SBEC_LAUNCH_CHECK();                                \
     } while (0)
 
-template <typename T, int F, bool HESS>
-static int launch_epi(const Geom& g, const Work& w, const XArgs& a, int ne, cudaStream_t s) {
-    auto kern = k_epilogue<T, F, HESS>;
+template <typename T, int F, bool HESS, int DC>
+static int launch_epi_dc(const Geom& g, const Work& w, const XArgs& a, int ne, cudaStream_t s) {
+    auto kern = k_epilogue<T, F, HESS, DC>;
     constexpr size_t smem = epi_smem<T, F, HESS>();
     static size_t granted = 0;
     if (int st = ensure_smem(kern, smem, granted)) return st;
@@ -1878,6 +1909,16 @@ static int launch_epi(const Geom& g, const Work& w, const XArgs& a, int ne, cuda
     kern<<<dim3(ne, g.nl), kEpiThreads, smem, s>>>(a, w.work, g.G);
     SBEC_LAUNCH_CHECK();
     return SBEC_OK;
+}
+
+// a.dens set (FP64 only): the gradient epilogue stores the densities, the Hessian
+// epilogue reads them
+template <typename T, int F, bool HESS>
+static int launch_epi(const Geom& g, const Work& w, const XArgs& a, int ne, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+        if (a.dens) return launch_epi_dc<T, F, HESS, HESS ? 2 : 1>(g, w, a, ne, s);
+    }
+    return launch_epi_dc<T, F, HESS, 0>(g, w, a, ne, s);
 }
 
 template <typename T>
@@ -1913,6 +1954,7 @@ static XArgs xargs(const Geom& g, const XCfg& c, const void* in, void* out, doub
     a.imap = g.imap;
     a.fp = FinProj{};
     a.fe = 0;
+    a.dens = nullptr;
     return a;
 }
 
@@ -1978,6 +2020,7 @@ static int grad_F(const Geom& g, const Work& w, const void* X, void* Geuc, void*
         XArgs a = xargs<T>(g, c, nullptr, gout, w.partA);
         a.X = X;
         a.fp = fg;
+        a.dens = w.dens;
         st = launch_epi<T, F, false>(g, w, a, ne, s);
         if (st) return st;
     }
@@ -2018,7 +2061,7 @@ static int energy_F(const Geom& g, const Work& w, const void* X, cudaStream_t s)
 
 template <typename T, int F>
 static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
-                  cudaStream_t s, int sigslot = -1) {
+                  cudaStream_t s, int sigslot, bool dens) {
     constexpr int C = 2 * F + 1;
     const int nb = SBEC_ELEM_GRID(g.G, (k_proj_apply<T, F, false>));
     const void* zin = Z;
@@ -2057,6 +2100,7 @@ static int hess_F(const Geom& g, const Work& w, const void* X, const void* Z, do
         XArgs a = xargs<T>(g, c, w.work, HZ, w.partA);
         a.X = X; a.Zd = zin; a.sigma = sigma; a.riem = riem; a.scal = w.scal; a.sigslot = sigslot;
         a.zproj = fuse ? 1 : 0;
+        if (dens) a.dens = w.dens;
         if (riem) a.fp = fpz;
         // inverse x-FFT in place, then the Hessian epilogue (split as in grad_F)
         st = launch_x<T, F, X_INV>(c, xargs<T>(g, c, w.work, w.work, nullptr), w, s);
@@ -2110,8 +2154,8 @@ int Ops<T>::grad(const Geom& g, const Work& w, const void* X, void* Geuc, void* 
 
 template <typename T>
 int Ops<T>::hessvec(const Geom& g, const Work& w, const void* X, const void* Z, double sigma, int riem, void* HZ,
-                    cudaStream_t s, int sigslot) {
-#define H_(F) hess_F<T, F>(g, w, X, Z, sigma, riem, HZ, s, sigslot)
+                    cudaStream_t s, int sigslot, bool dens) {
+#define H_(F) hess_F<T, F>(g, w, X, Z, sigma, riem, HZ, s, sigslot, dens)
     SBEC_DISPATCH_F(H_)
 #undef H_
 }

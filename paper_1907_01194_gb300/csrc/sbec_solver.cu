@@ -138,7 +138,7 @@ struct CgChunks {
             const int rr_now = par ? SL_RRB : SL_RRA, rr_next = par ? SL_RRA : SL_RRB;
             const sbec::CgSlots sl{SL_KAP, SL_ALPHA, rr_now, rr_next, SL_BETA, SL_J, SL_STOP, SL_MAXIN,
                                    SL_CG, SL_SEST, SL_CGNEG, SL_CGHD, kSkipCg};
-            int e = Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, cs, SL_SIG);
+            int e = Ops<T>::hessvec(g, w, u, p, 1.0, 1, Hp, cs, SL_SIG, true);
             if (!e) e = Ops<T>::cg_curv(g, w, p, Hp, sl, cs);
             if (!e) e = Ops<T>::cg_update(g, w, x, r, p, Hp, sl, cs);
             if (!e) e = lin(cs, p, r, 1.0, p, SL_BETA, -1, nullptr, SL_D0);
@@ -250,7 +250,7 @@ struct Solver {
     }
     int hess(const void* u, const void* z, double sigma, int riem, void* out) {
         ++st->n_hvp;
-        return Ops<T>::hessvec(g, w, u, z, sigma, riem, out, s);
+        return Ops<T>::hessvec(g, w, u, z, sigma, riem, out, s, -1, true);
     }
     int retract(const void* u, const void* xi, double t, void* out) {
         return Ops<T>::retract(g, w, u, xi, t, o.retraction, out, s);
@@ -815,7 +815,7 @@ struct BatchSolver {
                 TRY(Ops<T>::retract(g, w, u, x, 1.0, o.retraction, z, s, SL_T));
                 TRY(lin(r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));
                 for (int b = 0; b < B; ++b) ++st[b].n_hvp;
-                TRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s));
+                TRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s, -1, true));
                 TRY(Ops<T>::dot2(g, w, r, Hp, nullptr, nullptr, SL_MB, s));
                 TRY(pull());
                 bool more = false;
@@ -1642,7 +1642,7 @@ struct GraphBranch {
                 GTRY(while_node(1, c_ls, [&](cudaStream_t s2) -> int {
                     GTRY(Ops<T>::retract(g, w, u, x, 1.0, o.retraction, z, s2, SL_T));
                     GTRY(lin(s2, r, 1.0, z, -1.0, u, -1, -1, gE, r, SL_MA));
-                    GTRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s2));
+                    GTRY(Ops<T>::hessvec(g, w, u, r, 0.0, 0, Hp, s2, -1, true));
                     GTRY(Ops<T>::dot2(g, w, r, Hp, nullptr, nullptr, SL_MB, s2));
                     return ctlk(s2, G_ARNT_LS, c_ls, 0, 3);
                 }));

@@ -55,7 +55,7 @@ struct Tuner {
         for (int i = 0; i <= r; ++i) {
             if (i == 1 && cudaEventRecord(e0, s) != cudaSuccess) return SBEC_ERR_CUDA;
             int st = Ops<T>::grad(g, w, X, nullptr, h->stage[1], true, s);
-            if (!st) st = Ops<T>::hessvec(g, w, X, h->stage[1], 0.0, 1, h->stage[2], s);
+            if (!st) st = Ops<T>::hessvec(g, w, X, h->stage[1], 0.0, 1, h->stage[2], s, -1, true);
             if (st) return st;
         }
         float t = 0.f;

@@ -28,7 +28,9 @@ def test_flop_model(name):
     assert bench.flops_model(w, "x_fwd_energy") == C * rows_x * _fft(n[0]) + G * bench.PW_FLOPS["energy"][w.F]
     # epilogues: pointwise only
     assert bench.flops_model(w, "x_inv_grad") == G * bench.PW_FLOPS["grad"][w.F]
-    assert bench.flops_model(w, "x_inv_hess") == G * bench.PW_FLOPS["hess"][w.F]
+    # the FP64 Hessian epilogue reads the densities the gradient stored
+    assert bench.flops_model(w, "x_inv_hess") == G * (bench.PW_FLOPS["hess"][w.F] - bench.DENS_FLOPS[w.F])
+    assert 0 < bench.DENS_FLOPS[w.F] < bench.PW_FLOPS["energy"][w.F]
     m = n[-1]
     assert bench.flops_model(w, "s_k2") == C * (G // m) * (2 * _fft(m) + 4 * m)
     # batches scale linearly
@@ -61,7 +63,7 @@ def test_roofline_picks_the_longest_modelled_kernel():
     prof = {"x_inv_hess": (4.0, 1), "s_k2": (2.5, 2), "finalize": (9.0, 3)}
     r = bench.roofline_of(prof, w, "fp64", 1, w.name)
     assert r["kernel"] == "x_inv_hess" and r["bound"] == "alu"
-    fl = math.prod(w.n) * bench.PW_FLOPS["hess"][w.F]
+    fl = math.prod(w.n) * (bench.PW_FLOPS["hess"][w.F] - bench.DENS_FLOPS[w.F])
     assert r["achieved"] == pytest.approx(fl / 4.0e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_NOMINAL_GFLOPS)
     # with a measured FP64 rate the fraction is of that rate

@@ -107,6 +107,6 @@ def test_spin3_2d_table_energies(case, M, dev):
 @pytest.mark.parametrize("M", [0.0, 0.5, 1.5])
 def test_spin3_3d_case1_table_energies(M, dev):
     printed = _printed("spin3_2d_3d_energies.txt")[(3, 1, M)]
-    st = _cascadic(lambda n: W.paper_spin3_3d(1, M, n), 128, dev, mixed=True)
+    st = _cascadic(lambda n: W.paper_spin3_3d(1, M, n), 128, dev)
     assert st["converged"]
     assert abs(st["energy"] - printed) <= 1e-4, (st["energy"], printed)

@@ -228,6 +228,36 @@ def test_host_riemannian_hessvec_uses_the_gradient_at_the_same_pointer(dev):
     assert np.array_equal(Hd.cpu().numpy(), Hh2)
 
 
+@pytest.mark.parametrize("w", [CASES[2], CASES[3], CASES[4], CASES[5], CASES[11]], ids=lambda w: w.name)
+def test_hessian_reads_the_densities_of_the_gradient_at_the_same_state(w, dev):
+    # FP64 handles in 2D / 3D: a Hessian-vector product at the X of the latest
+    # gradient reads the densities that gradient stored; at any other X it forms them.
+    # Both against the oracle, and the stored densities of another state are not used
+    sbec = _sbec()
+    P, u, Xf, Zf = case_inputs(w)
+    X = torch.from_numpy(Xf).to(dev)
+    Z = torch.from_numpy(Zf).to(dev)
+    X2 = torch.from_numpy(W.initial_fields(w, seed=12345)).to(dev)
+    Hf, Hc, Ho, Hr = (torch.empty_like(X) for _ in range(4))
+    with sbec.Handle.from_workload(w) as h:
+        h.hessvec(X, Z, Hf, sigma=0.1, riemannian=False)          # no gradient yet: formed
+        h.grad(X2)                                                # densities of X2 stored
+        h.hessvec(X, Z, Ho, sigma=0.1, riemannian=False)          # another state: formed
+        h.grad(X)
+        h.hessvec(X, Z, Hc, sigma=0.1, riemannian=False)          # read
+        h.hessvec(X, Z, Hr, sigma=0.1, riemannian=True)           # read
+        h.sync()
+    Xm, Zm = O.from_u(P, u), O.to_matrix(P, Zf)
+    H_ref = O.to_fields(P, O.hessvec(P, Xm, Zm) + 0.1 * Zm)
+    for H in (Hf, Hc, Ho):
+        assert rel(H.cpu().numpy(), H_ref) <= 1e-12
+    assert torch.equal(Hf, Ho)
+    assert rel(Hc.cpu().numpy(), Hf.cpu().numpy()) <= 1e-14
+    g = O.to_u(P, O.gradient(P, Xm))
+    Hr_ref = O.rhess(P, u, O.to_u(P, Zm), g=g, sigma=0.1)
+    assert rel(Hr.cpu().numpy(), O.to_fields(P, O.from_u(P, Hr_ref))) <= 1e-11
+
+
 def test_deterministic_repeat(dev):
     sbec = _sbec()
     w = CASES[5]
