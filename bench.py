@@ -31,6 +31,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from dataclasses import replace
 
 import numpy as np
 
@@ -100,7 +101,15 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--tiles", default=None,
                     help="launch shapes as JSON (keys of sbec_tune) instead of autotuning, e.g. for profiling")
-    return ap.parse_args()
+    ap.add_argument("--grid", default=None,
+                    help="the workload's problem on another grid, e.g. 128,128,256: a small case of the same "
+                         "kernels for profiling (evaluation rate only: no solves, no CPU baseline)")
+    args = ap.parse_args()
+    if args.grid:
+        if args.workload == "batch512":
+            ap.error("--grid applies to the single-problem workloads")
+        args.no_solve = args.no_cpu_baseline = True
+    return args
 
 
 def dist_setup():
@@ -396,6 +405,9 @@ def run_ours(args, world, rank, local):
         nstates = 1
     else:
         w_main = workload(args.workload)
+        if args.grid:
+            w_main = w_main.at(tuple(int(v) for v in args.grid.split(",")))
+            w_main = replace(w_main, name=f"{w_main.name}_on_{'x'.join(str(v) for v in w_main.n)}")
         wname = w_main.name
         h = sbec.Handle.from_workload(w_main, precision=args.precision, stream=stream.cuda_stream)
         sbytes = w_main.C * w_main.G * elem

@@ -101,7 +101,9 @@ int sbec_energy(sbec_handle* h, const void* X, double* E);
  * G_riem, with u the real stacking of X (Sec. 4).  Either output may be NULL.
  * E and rgrad_norm (||grad E||_2, the stopping norm of Sec. 7.1) are optional
  * host outputs.  The Lemma 4.1 coefficients are cached in the handle for the
- * next sbec_hessvec with riemannian != 0. */
+ * next sbec_hessvec with riemannian != 0; FP64 handles in 2D and 3D also keep
+ * the pointwise densities of X (rho, F_z, F_+, A00, A_2l; Sec. 2) for the
+ * Hessian-vector products at the same X pointer. */
 int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* E,
               double* rgrad_norm);
 
@@ -111,7 +113,9 @@ int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* 
  * - alpha_g xi - beta_g Gamma xi) with xi = P_u Z, using the alpha_g, beta_g
  * of the latest sbec_grad call at the same X pointer, host or device (the call
  * recomputes them when X differs from that call's pointer; after changing the
- * contents of X in place, call sbec_grad again). */
+ * contents of X in place, call sbec_grad again).  Either form, at the X pointer
+ * of the latest sbec_grad, reads the densities that call kept (FP64, 2D/3D)
+ * instead of forming them again. */
 int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int riemannian,
                  void* HZ);
 

@@ -880,8 +880,8 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilo
     for (int k = 0; k < NS - 1; ++k) issue(pt + k * stride, k);
     for (int k = 0; pt < G; ++k, pt += stride) {
         issue(pt + (NS - 1) * stride, (k + NS - 1) % NS);
-        Dens<F, T2> D;
-        if constexpr (DC == 2) dens_load<F>(D, dens + pt, G);    // in flight during the wait
+        Dens<F, T2> Dl;                              // DC == 2: loads in flight during the wait
+        if constexpr (DC == 2) dens_load<F>(Dl, dens + pt, G);
         cp_async_wait<NS - 1>();                     // this thread's copies of point pt are in
         const int sk = k % NS;
         const T2* sx = stg + (size_t)sk * NA * C * P + tid;
@@ -889,7 +889,9 @@ __global__ void __launch_bounds__(kEpiThreads, EpiBlocks<T, F, HESS>::v) k_epilo
 #pragma unroll
         for (int c = 0; c < C; ++c) { x[c] = sx[c * P]; l[c] = sx[(C + c) * P]; }
         const T V = vst[sk * P + tid];
-        if constexpr (DC != 2) D.compute(x);
+        Dens<F, T2> D;
+        if constexpr (DC == 2) D = Dl;
+        else D.compute(x);
         if constexpr (DC == 1) dens_store<F>(D, dens + pt, G);
         if (!HESS) {
             grad_point<F, T2>(x, D, V, pp, l, o);

@@ -114,9 +114,17 @@ __global__ void __launch_bounds__(kTmaW * Split2<LOGN>::N1, 1)
     T2* in = reinterpret_cast<T2*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));   // [NS][N][W]
     T2* ex = in + NS * TILE;                         // [N2][RS]
     __shared__ __align__(8) uint64_t bar[NS];
+    // the pass's twiddles W_N^j and (S_K2, S_PARSEVAL) its axis's k-space factors,
+    // read by every tile: in shared memory once per block (a warp shares one q, so
+    // each read is a broadcast) instead of a global load per element and tile
+    __shared__ T2 tw[N];
+    __shared__ T fe[N];
     const int tid = threadIdx.x, w = tid & (W - 1), q = tid / W;
-    const T2* __restrict__ tw = reinterpret_cast<const T2*>(a.tw);
     const long long stride = gridDim.x;
+    for (int j = tid; j < N; j += blockDim.x) {
+        tw[j] = reinterpret_cast<const T2*>(a.tw)[j];
+        if (MODE == S_K2 || MODE == S_PARSEVAL) fe[j] = reinterpret_cast<const T*>(a.k2t[a.axis])[j];
+    }
 
     // thread 0's bookkeeping: loads issued into / consumed from each stage (the
     // pending load of stage s completes phase (consumed[s] & 1) of its mbarrier),
@@ -196,7 +204,6 @@ __global__ void __launch_bounds__(kTmaW * Split2<LOGN>::N1, 1)
                 const bool ya = (a.axis == 1);
                 const T f0 = reinterpret_cast<const T*>(a.k2t[0])[ix] +
                              reinterpret_cast<const T*>(a.k2t[ya ? 2 : 1])[o];
-                const T* __restrict__ fe = reinterpret_cast<const T*>(a.k2t[a.axis]);
 #pragma unroll
                 for (int k1 = 0; k1 < N1; ++k1) {
                     const T f = f0 + fe[q + N2 * k1];
