@@ -259,7 +259,11 @@ const double* sbec_scalars(const sbec_handle* h);
  * block of the x-axis FFT pass, a power of 2 dividing the rows of an
  * instance.  s_pencils[a], a = 1, 2: pencils (consecutive x columns) per
  * shared-memory tile of the FFT pass along axis a, a power of 2 <= n[0];
- * s_split[a]: butterflies per thread of that pass (1, 2, 4 or 8).
+ * s_split[a]: butterflies per thread of that pass (1, 2, 4 or 8), or 16 for
+ * the TMA pass (SBEC_MIXED handles of one instance, an axis of 128 or 256
+ * points: tiles moved by cp.async.bulk.tensor, s_pencils[a] = 8, 16 or 32
+ * columns per tile, n[0] a multiple of it; the built-in choice there, with
+ * 8 columns on the last axis and 16 on the middle one of a 3D problem).
  * elem_per_sm: blocks per SM of the grid-stride elementwise and reduction
  * kernels (1..32); a kernel of which fewer blocks fit per SM gets whole waves
  * of the blocks that fit.  At most 16384 points per FFT block and 227 KB of shared

@@ -17,6 +17,9 @@ constexpr int kMaxC = 2 * kMaxF + 1;
 // rho, F_z, F_+ (2), and for F = 2, 4 the singlet amplitude A00 (2), for F = 3
 // A00 and the five quintet amplitudes A_{2l} (2 each)
 __host__ __device__ constexpr int dens_count(int F) { return F == 1 ? 4 : F == 3 ? 16 : 6; }
+// sbec_tune s_split value that selects the TMA strided pass (FP32, one instance),
+// its tile width being s_pencils (8, 16 or 32 columns)
+constexpr int kTmaSplit = 16;
 
 // device scalar-block slots beyond the public SBEC_S_* ones
 enum {

@@ -1821,36 +1821,49 @@ static EncodeTiledFn tma_encoder() {
 
 // The field at `base` as a 4D float tensor [C][n_z][n_y][2 n_x] with a box of one
 // tile of the pass along `axis` (2W floats along x, the whole axis).
-static bool tma_map(CUtensorMap* m, const void* base, const Geom& g, int axis) {
+static bool tma_map(CUtensorMap* m, const void* base, const Geom& g, int axis, int W) {
     EncodeTiledFn enc = tma_encoder();
     if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
     const cuuint64_t nx2 = 2ull * (cuuint64_t)g.n[0];
     const cuuint64_t dims[4] = {nx2, (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)g.C};
     const cuuint64_t strides[3] = {nx2 * 4, nx2 * g.n[1] * 4, nx2 * g.n[1] * g.n[2] * 4};
-    const cuuint32_t box[4] = {2u * kTmaW, axis == 1 ? (cuuint32_t)g.n[1] : 1u, axis == 2 ? (cuuint32_t)g.n[2] : 1u,
-                               1u};
+    const cuuint32_t box[4] = {2u * (cuuint32_t)W, axis == 1 ? (cuuint32_t)g.n[1] : 1u,
+                               axis == 2 ? (cuuint32_t)g.n[2] : 1u, 1u};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// the pass runs on the TMA kernel: FP32, one instance, the built-in tile width,
-// a pass axis of 128 or 256 points and x a multiple of the tile width
-template <typename T>
-static bool tma_pass(const Geom& g, int axis) {
-    if (sizeof(T) != 4 || g.B != 1 || g.nl != 1 || g.imap || g.dim < 2) return false;
-    if (g.n[axis] != 128 && g.n[axis] != 256) return false;
-    if (g.n[0] % kTmaW != 0) return false;
-    if (g.tune.s_pencils[axis] != 0 && g.tune.s_pencils[axis] != kTmaW) return false;
-    return tma_encoder() != nullptr;
+// TMA tile width of a pass with launch shapes t (0: not a TMA shape): s_split =
+// kTmaSplit with s_pencils 8, 16 or 32, or both 0 (the built-in choice: 8 columns
+// on the last axis, whose fused fwd·|k|²·inv and Parseval passes were measured
+// fastest at four blocks per SM, 16 on the middle axis of a 3D problem)
+static int tma_width(const Tune& t, int axis, int dim) {
+    const int W = t.s_pencils[axis], sp = t.s_split[axis];
+    const int wdef = axis == dim - 1 ? 8 : 16;
+    if (W == 0 && sp == 0) return wdef;
+    if (sp != kTmaSplit) return 0;
+    return (W == 8 || W == 16 || W == 32) ? W : (W == 0 ? wdef : 0);
 }
 
-template <int MODE, int LOGN>
+// the pass's TMA tile width, or 0 where the pass does not run on the TMA kernel:
+// FP32, one instance, a TMA shape, a pass axis of 128 or 256 points and x a
+// multiple of the tile width
+template <typename T>
+static int tma_pass(const Geom& g, int axis) {
+    if (sizeof(T) != 4 || g.B != 1 || g.nl != 1 || g.imap || g.dim < 2) return 0;
+    if (g.n[axis] != 128 && g.n[axis] != 256) return 0;
+    const int W = tma_width(g.tune, axis, g.dim);
+    if (W == 0 || g.n[0] % W != 0) return 0;
+    return tma_encoder() != nullptr ? W : 0;
+}
+
+template <int MODE, int LOGN, int W>
 static int launch_tma_n(const Geom& g, const SArgs& a, const Work& w, cudaStream_t s) {
-    auto kern = k_spass_tma<MODE, LOGN>;
-    constexpr size_t smem = tma_smem_bytes<LOGN>();
-    constexpr int nth = kTmaW * Split2<LOGN>::N1;
+    auto kern = k_spass_tma<MODE, LOGN, W>;
+    constexpr size_t smem = tma_smem_bytes<LOGN, W>();
+    constexpr int nth = W * Split2<LOGN>::N1;
     static size_t granted = 0;
     if (int st = ensure_smem(kern, smem, granted)) return st;
     static std::atomic<int> occ{0};
@@ -1863,8 +1876,8 @@ static int launch_tma_n(const Geom& g, const SArgs& a, const Work& w, cudaStream
         occ.store(per_sm, std::memory_order_relaxed);
     }
     CUtensorMap mi, mo;
-    if (!tma_map(&mi, a.in, g, a.axis)) return SBEC_ERR_CUDA;
-    if (!tma_map(&mo, a.out ? a.out : a.in, g, a.axis)) return SBEC_ERR_CUDA;
+    if (!tma_map(&mi, a.in, g, a.axis, W)) return SBEC_ERR_CUDA;
+    if (!tma_map(&mo, a.out ? a.out : a.in, g, a.axis, W)) return SBEC_ERR_CUDA;
     TmaArgs ta;
     ta.s = a;
     ta.ntiles = (long long)g.C * a.nouter * a.ntx;
@@ -1881,14 +1894,16 @@ static int launch_tma_n(const Geom& g, const SArgs& a, const Work& w, cudaStream
 // two-level / Stockham kernels
 template <typename T, int MODE>
 static int launch_pass(const Geom& g, const SCfg& c, const SArgs& a, const Work& w, cudaStream_t s) {
-    if (tma_pass<T>(g, a.axis)) {
-        if (a.W != kTmaW) {
-            SArgs b = a;
-            b.W = kTmaW;
-            b.ntx = g.n[0] / kTmaW;
-            return g.n[a.axis] == 256 ? launch_tma_n<MODE, 8>(g, b, w, s) : launch_tma_n<MODE, 7>(g, b, w, s);
+    if (const int W = tma_pass<T>(g, a.axis)) {
+        SArgs b = a;
+        b.W = W;
+        b.ntx = g.n[0] / W;
+        const bool n256 = g.n[a.axis] == 256;
+        switch (W) {
+            case 8: return n256 ? launch_tma_n<MODE, 8, 8>(g, b, w, s) : launch_tma_n<MODE, 7, 8>(g, b, w, s);
+            case 16: return n256 ? launch_tma_n<MODE, 8, 16>(g, b, w, s) : launch_tma_n<MODE, 7, 16>(g, b, w, s);
+            default: return n256 ? launch_tma_n<MODE, 8, 32>(g, b, w, s) : launch_tma_n<MODE, 7, 32>(g, b, w, s);
         }
-        return g.n[a.axis] == 256 ? launch_tma_n<MODE, 8>(g, a, w, s) : launch_tma_n<MODE, 7>(g, a, w, s);
     }
     return launch_s<T, MODE>(c, a, w, s);
 }
@@ -2339,6 +2354,14 @@ bool Ops<T>::tune_ok(const Geom& g, const Tune& t) {
     for (int ax = 1; ax < 3; ++ax) {
         const int W = t.s_pencils[ax], sp = t.s_split[ax];
         if (ax >= g.dim && (W != 0 || sp != 0)) return false;
+        if (sp == kTmaSplit) {
+            // the TMA pass: a width it has, on a pass it runs
+            if (W != 0 && W != 8 && W != 16 && W != 32) return false;
+            Geom h = g;
+            h.tune = t;
+            if (!tma_pass<T>(h, ax)) return false;
+            continue;
+        }
         if (sp != 0 && sp != 1 && sp != 2 && sp != 4 && sp != 8) return false;
         if (W == 0) continue;
         if (!pow2(W) || W > g.n[0]) return false;
@@ -2361,8 +2384,13 @@ Tune Ops<T>::resolved(const Geom& g, int num_sms) {
     Tune t{};
     t.x_rows = xcfg<T>(g).rpb;
     for (int ax = 1; ax < g.dim; ++ax) {
-        // the TMA pass takes the built-in choice where it applies (its tile is kTmaW wide)
-        t.s_pencils[ax] = tma_pass<T>(g, ax) ? kTmaW : scfg<T>(g, ax, num_sms).W;
+        // the TMA pass (its tile width, and s_split = kTmaSplit) where it runs
+        if (const int W = tma_pass<T>(g, ax)) {
+            t.s_pencils[ax] = W;
+            t.s_split[ax] = kTmaSplit;
+            continue;
+        }
+        t.s_pencils[ax] = scfg<T>(g, ax, num_sms).W;
         t.s_split[ax] = g.tune.s_split[ax] > 0 ? g.tune.s_split[ax] : 1;
     }
     t.elem_per_sm = g.tune.elem_per_sm > 0 ? g.tune.elem_per_sm : 8;

@@ -84,7 +84,7 @@ struct Tuner {
         // candidate values per field, in the struct's order
         const int rows[] = {1, 2, 4, 8, 16, 32, 64};
         const int pencils[] = {1, 2, 4, 8, 16, 32, 64};
-        const int splits[] = {1, 2, 4};
+        const int splits[] = {1, 2, 4, sbec::kTmaSplit};
         const int per_sm[] = {2, 4, 8, 16, 32};
         // field(t) is the member of t under trial
         auto try_field = [&](auto field, const int* cand, int nc) -> int {
@@ -105,7 +105,7 @@ struct Tuner {
         int st = try_field([](Tune& t) -> int& { return t.x_rows; }, rows, 7);
         for (int a = 1; a < g.dim && !st; ++a) {
             st = try_field([a](Tune& t) -> int& { return t.s_pencils[a]; }, pencils, 7);
-            if (!st) st = try_field([a](Tune& t) -> int& { return t.s_split[a]; }, splits, 3);
+            if (!st) st = try_field([a](Tune& t) -> int& { return t.s_split[a]; }, splits, 4);
         }
         if (!st) st = try_field([](Tune& t) -> int& { return t.elem_per_sm; }, per_sm, 5);
         if (st) return st;

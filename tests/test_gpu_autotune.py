@@ -98,6 +98,7 @@ def test_invalid_shapes_are_rejected(dev):
         before = h.get_tune()
         for bad in (dict(x_rows=3), dict(x_rows=16), dict(s_pencils=[0, 128, 0]), dict(s_pencils=[0, 3, 0]),
                     dict(s_split=[0, 3, 0]), dict(s_pencils=[0, 0, 4]), dict(s_pencils=[2, 0, 0]),
+                    dict(s_pencils=[0, 16, 0], s_split=[0, 16, 0]),     # the TMA pass: FP32 only
                     dict(elem_per_sm=33), dict(elem_per_sm=-1)):
             with pytest.raises(sbec.SbecError):
                 h.set_tune(bad)
@@ -119,3 +120,29 @@ def test_batch_autotune_matches_single_instances(dev):
         P = O.Problem(F=w.F, n=w.n, lo=w.lo, hi=w.hi, beta=w.beta, V=W.potential(w), M=w.M)
         E_ref = O.energy(P, O.to_matrix(P, X0[i]))
         assert abs(Eb[i] - E_ref) <= 1e-12 * abs(E_ref)
+
+
+def test_tma_pass_shapes_on_mixed_handles(dev):
+    # FP32 passes along 128- or 256-point axes default to the TMA kernel with 16-column
+    # tiles on the middle axis and 8-column tiles on the last (s_split = 16 marks the
+    # TMA pass, s_pencils its width); widths other than
+    # 8, 16, 32 are rejected, and the tuner may move between TMA widths and the
+    # register kernels
+    from paper_1907_01194_gb300 import sbec
+    w = _wl(2, (32, 128, 128), 8.0, 0.3, (150.0, 4.0, -3.0, 0), lattice=6.0)
+    with sbec.Handle.from_workload(w, precision="mixed") as h:
+        t0 = h.get_tune()
+        assert t0["s_pencils"][1:] == [16, 8] and t0["s_split"][1:] == [16, 16]
+        for bad in (dict(s_pencils=[0, 4, 0], s_split=[0, 16, 0]), dict(s_pencils=[0, 64, 0], s_split=[0, 16, 0])):
+            with pytest.raises(sbec.SbecError):
+                h.set_tune(bad)
+            assert h.get_tune() == t0
+        X = torch.from_numpy(W.initial_fields(w).astype(np.complex64)).to(dev)
+        t = h.autotune(X, reps=2)
+        got = h.get_tune()
+        for k in ("x_rows", "s_pencils", "s_split", "elem_per_sm"):
+            assert got[k] == t[k]
+        for ax in (1, 2):
+            assert t["s_split"][ax] in (1, 2, 4, 16)
+            if t["s_split"][ax] == 16:
+                assert t["s_pencils"][ax] in (8, 16, 32)

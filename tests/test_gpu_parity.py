@@ -136,16 +136,38 @@ def test_mixed_precision_bound(w, dev):
     assert rel(H1.cpu().numpy(), O.to_fields(P, O.hessvec(P, Xm, Zm))) <= 2e-5
 
 
+def _tma_tiles(w, width):
+    # launch shapes with the TMA pass of the given tile width on every axis it runs on
+    # (128 or 256 points), None when x is not a multiple of the width
+    if w.n[0] % width:
+        return None
+    pen, spl = [0, 0, 0], [0, 0, 0]
+    for ax in range(1, w.dim):
+        if w.n[ax] in (128, 256):
+            pen[ax], spl[ax] = width, 16
+    return dict(s_pencils=pen, s_split=spl)
+
+
+@pytest.mark.parametrize("width", [8, 16, 32])
 @pytest.mark.parametrize("w", TMA_CASES, ids=lambda w: w.name)
-def test_mixed_riemannian_and_repeatable_on_tma_passes(w, dev):
-    # the Riemannian products through the TMA passes, and bitwise repeatability of
-    # the persistent tile loop (fixed tile order per block, fixed reduction order)
+def test_mixed_riemannian_and_repeatable_on_tma_passes(w, width, dev):
+    # the Riemannian products through the TMA passes of each tile width (8, 16, 32
+    # columns: 4, 2, 1 blocks per SM), and bitwise repeatability of the persistent
+    # tile loop (fixed tile order per block, fixed reduction order)
     sbec = _sbec()
+    tiles = _tma_tiles(w, width)
+    if tiles is None:
+        pytest.skip(f"n_x = {w.n[0]} is not a multiple of the tile width {width}")
     P, u, Xf, Zf = case_inputs(w)
     X = torch.from_numpy(Xf.astype(np.complex64)).to(dev)
     Z = torch.from_numpy(Zf.astype(np.complex64)).to(dev)
     Gr, H1, H2 = (torch.empty_like(X) for _ in range(3))
     with sbec.Handle.from_workload(w, precision="mixed") as h:
+        h.set_tune(tiles)
+        got = h.get_tune()
+        for ax in range(1, w.dim):
+            if tiles["s_split"][ax]:
+                assert (got["s_pencils"][ax], got["s_split"][ax]) == (width, 16), got
         E1 = h.energy(X)
         E2, rn = h.grad(X, G_riem=Gr)
         h.hessvec(X, Z, H1, sigma=0.2, riemannian=True)
