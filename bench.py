@@ -635,6 +635,10 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
                    "max_outer": int(max(s["outer_iters"] for s in sts)),
                    "max_inner": int(max(s["inner_iters"] for s in sts)),
                    "energies_head": [s["energy"] for s in sts[:3]]}
+            # the instances of the class whose oracle ground state is stored (a seeded sample)
+            gold = {x.name: golden_ground_state(x.name) for x in ws}
+            cls["oracle_sample_fp64_rel_err"] = {x.name: abs(s["energy"] - gold[x.name]) / abs(gold[x.name])
+                                                 for x, s in zip(ws, sts) if gold[x.name] is not None}
             del ws_buf
             if args.precision == "fp64":
                 # mixed form of the same class: FP32 lock-step solve, FP64 refinement
@@ -652,7 +656,9 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
                 cls["mixed_refined"] = {
                     "seconds": dm, "converged": int(sum(s["converged"] for s in sf)),
                     "max_energy_rel_diff": max(abs(a["energy"] - b["energy"]) / abs(b["energy"])
-                                               for a, b in zip(sf, sts))}
+                                               for a, b in zip(sf, sts)),
+                    "oracle_sample_rel_err": {x.name: abs(s["energy"] - gold[x.name]) / abs(gold[x.name])
+                                              for x, s in zip(ws, sf) if gold[x.name] is not None}}
             out["classes"].append(cls)
         out["fp64" if args.precision == "fp64" else "mixed"] = {"seconds": t_all}
         # the same solves as ONE device-driven graph launch over the three size classes
@@ -747,7 +753,8 @@ def time_to_ground_state(args, sbec, torch, dev, stream, groups, w):
                                                                 "n_hvp")},
                               "converged": bool(sf["converged"])},
             "speedup_mixed_over_fp64": t64 / tmx if tmx > 0 else None,
-            "energy_rel_diff": abs(sf["energy"] - s64["energy"]) / abs(s64["energy"])}
+            "energy_rel_diff": abs(sf["energy"] - s64["energy"]) / abs(s64["energy"]),
+            "oracle": gold_report(golden_ground_state(w.name), {"fp64": s64["energy"], "mixed_refined": sf["energy"]})}
 
 
 # The paper's spin-2 2D case (Sec. 7.1, table of spin-2 results in 2D, ARNT with R1):

@@ -115,7 +115,8 @@ int sbec_grad(sbec_handle* h, const void* X, void* G_euc, void* G_riem, double* 
  * recomputes them when X differs from that call's pointer; after changing the
  * contents of X in place, call sbec_grad again).  Either form, at the X pointer
  * of the latest sbec_grad, reads the densities that call kept (FP64, 2D/3D)
- * instead of forming them again. */
+ * instead of forming them again, and a host X that call staged is not copied
+ * to the device again while no other call has used the staging field. */
 int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int riemannian,
                  void* HZ);
 

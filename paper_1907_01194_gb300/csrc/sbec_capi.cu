@@ -79,7 +79,10 @@ constexpr size_t kInPlaceHostBytes = size_t(1) << 20;
 
 // Resolve an input array: device pointers pass through; host arrays are read in
 // place (page-locked and small) or copied into staging buffer `slot`.
-int stage_in(sbec_handle* h, const void* p, int slot, const void** out, bool* host) {
+// reuse (slot 0 only): the caller's contract says p's contents are those stage[0]
+// received from p last (sbec_hessvec at the X of the latest sbec_grad), so that
+// copy is not repeated
+int stage_in(sbec_handle* h, const void* p, int slot, const void** out, bool* host, bool reuse = false) {
     if (!p) { *out = nullptr; return SBEC_ERR_ARG; }
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
@@ -93,7 +96,12 @@ int stage_in(sbec_handle* h, const void* p, int slot, const void** out, bool* ho
         *out = attr.devicePointer;
         return SBEC_OK;
     }
+    if (slot == 0) {
+        if (reuse && p == h->stage0_src) { *out = h->stage[0]; return SBEC_OK; }
+        h->stage0_src = nullptr;
+    }
     TRY_CUDA(cudaMemcpyAsync(h->stage[slot], p, h->field_bytes, cudaMemcpyHostToDevice, h->stream));
+    if (slot == 0) h->stage0_src = p;
     *out = h->stage[slot];
     return SBEC_OK;
 }
@@ -464,7 +472,9 @@ int sbec_hessvec(sbec_handle* h, const void* X, const void* Z, double sigma, int
     if (!h || !X || !Z || !HZ) return SBEC_ERR_ARG;
     bool host = false;
     const void *Xd, *Zd;
-    int st = stage_in(h, X, 0, &Xd, &host);
+    // X unchanged since the latest sbec_grad at the same pointer (the call's contract):
+    // a host X staged by that call is still in stage[0] unless another call replaced it
+    int st = stage_in(h, X, 0, &Xd, &host, h->last_grad_X == X);
     if (st) return st;
     st = stage_in(h, Z, 1, &Zd, &host);
     if (st) return st;

@@ -19,6 +19,7 @@ struct sbec_handle {
     double* d_lam2;
     void* d_V;
     void* stage[3];
+    const void* stage0_src;   // host array whose contents stage[0] received last (null: none known)
     double* h_scal;       // pinned mirror of the scalar block
     const void* last_grad_X;
     sbec::Prof prof;

@@ -991,6 +991,7 @@ int solve_one(sbec_handle* h, void* X, const sbec_solve_opts* opts, void* worksp
     void* Xd = X;
     if (host) {
         Xd = h->stage[0];
+        h->stage0_src = nullptr;     // the solve changes the staged copy
         if (cudaMemcpyAsync(Xd, X, h->field_bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
             return SBEC_ERR_CUDA;
     }
@@ -1083,6 +1084,7 @@ int sbec_prolongate(sbec_handle* hc, const void* Xc, sbec_handle* hf, void* Xf) 
     const void* Xcd = Xc;
     if (!sbec_is_device_ptr(Xc)) {
         host = true;
+        hc->stage0_src = nullptr;
         if (cudaMemcpyAsync(hc->stage[0], Xc, hc->field_bytes, cudaMemcpyHostToDevice, hc->stream) != cudaSuccess)
             return SBEC_ERR_CUDA;
         Xcd = hc->stage[0];

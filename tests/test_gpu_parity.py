@@ -243,11 +243,16 @@ def test_host_riemannian_hessvec_uses_the_gradient_at_the_same_pointer(dev):
         h.hessvec(X, Z, Hd, sigma=0.2, riemannian=True)
         h.sync()
         h.grad(Xh)                                           # cached for the host pointer Xh
-        h.hessvec(Xh, Zh, Hh1, sigma=0.2, riemannian=True)
+        h.hessvec(Xh, Zh, Hh1, sigma=0.2, riemannian=True)  # Xh's staged copy reused
         Xh2 = np.array(Xf, copy=True)                        # another pointer: recomputed
         h.hessvec(Xh2, Zh, Hh2, sigma=0.2, riemannian=True)
+        h.grad(Xh)
+        h.energy(np.array(Zf, copy=True))                    # another host array through the staging
+        Hh3 = np.empty_like(Xf)
+        h.hessvec(Xh, Zh, Hh3, sigma=0.2, riemannian=True)  # Xh staged again
     assert np.array_equal(Hd.cpu().numpy(), Hh1)
     assert np.array_equal(Hd.cpu().numpy(), Hh2)
+    assert np.array_equal(Hd.cpu().numpy(), Hh3)
 
 
 @pytest.mark.parametrize("w", [CASES[2], CASES[3], CASES[4], CASES[5], CASES[11]], ids=lambda w: w.name)
