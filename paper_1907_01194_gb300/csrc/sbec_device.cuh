@@ -355,6 +355,112 @@ template <typename T2, bool INV> struct RegDft<T2, 16, INV> {
     }
 };
 
+// FP64 16-point DFT with the stage-2 twiddles folded into the butterflies.  A
+// twiddle w = wr + i wi is written w = m (1 + i r) (r = wi / wr, |wr| >= |wi|) or
+// w = m (r + i) (r = wr / wi, otherwise), so that b w = m b' with b' = b (1 + i r)
+// or b (r + i) two FMAs; the real factor m then enters the butterfly's additions
+// as FMAs (a0 +- m2 b2', and m1 b1' +- m3 b3' from one product).  With |r| <= 1
+// every FMA has a bounded coefficient (the tangent / cotangent form of Linzer and
+// Feig's FMA butterflies).  Per row of four outputs this takes 24 FP64
+// instructions instead of 28 (three complex products and eight additions); the
+// FP64 passes are bound by the FP64 pipe, where instructions are the cost.
+template <bool INV, int E> struct W16Fold {
+    static constexpr double cs[16] = {1, kC8, kR2, kS8, 0, -kS8, -kR2, -kC8, -1, -kC8, -kR2, -kS8, 0, kS8, kR2, kC8};
+    static constexpr double sn[16] = {0, kS8, kR2, kC8, 1, kC8, kR2, kS8, 0, -kS8, -kR2, -kC8, -1, -kC8, -kR2, -kS8};
+    static constexpr double wr = cs[E & 15];
+    static constexpr double wi = INV ? sn[E & 15] : -sn[E & 15];
+    static constexpr bool tangent = (wr < 0 ? -wr : wr) >= (wi < 0 ? -wi : wi);
+    static constexpr double m = tangent ? wr : wi;
+    static constexpr double r = tangent ? wi / wr : wr / wi;
+};
+// b' with b w = m b'
+template <bool INV, int E>
+__device__ __forceinline__ double2 fold_w16(double2 b) {
+    using W = W16Fold<INV, E>;
+    if constexpr (W::tangent)
+        return make_double2(fma(-W::r, b.y, b.x), fma(W::r, b.x, b.y));      // b (1 + i r)
+    else
+        return make_double2(fma(W::r, b.x, -b.y), fma(W::r, b.y, b.x));      // b (r + i)
+}
+// one stage-2 row: DFT4 of (a0, b1 w^E1, b2 w^E2, b3 w^E3) in place, E2 = 2 E1, E3 = 3 E1
+template <bool INV, int E1>
+__device__ __forceinline__ void dft4_folded(double2& a0, double2& b1, double2& b2, double2& b3) {
+    constexpr int E2 = 2 * E1, E3 = 3 * E1;
+    using W1 = W16Fold<INV, E1>;
+    using W2 = W16Fold<INV, E2>;
+    using W3 = W16Fold<INV, E3>;
+    double2 t0, t1;
+    if constexpr ((E2 & 15) == 4 || (E2 & 15) == 12) {
+        const double2 a2 = mul_w16<double2, INV, E2>(b2);                   // +-i: no arithmetic
+        t0 = cadd(a0, a2);
+        t1 = csub(a0, a2);
+    } else {
+        const double2 c2 = fold_w16<INV, E2>(b2);
+        t0 = make_double2(fma(W2::m, c2.x, a0.x), fma(W2::m, c2.y, a0.y));
+        t1 = make_double2(fma(-W2::m, c2.x, a0.x), fma(-W2::m, c2.y, a0.y));
+    }
+    const double2 c1 = fold_w16<INV, E1>(b1), c3 = fold_w16<INV, E3>(b3);
+    const double2 p = make_double2(W1::m * c1.x, W1::m * c1.y);
+    const double2 t2 = make_double2(fma(W3::m, c3.x, p.x), fma(W3::m, c3.y, p.y));
+    const double2 t3 = mul_w16<double2, INV, 4>(make_double2(fma(-W3::m, c3.x, p.x), fma(-W3::m, c3.y, p.y)));
+    a0 = cadd(t0, t2);
+    b2 = csub(t0, t2);
+    b1 = cadd(t1, t3);
+    b3 = csub(t1, t3);
+}
+// FP64 8-point DFT, radix 2 x 4 with the W8 twiddles folded the same way
+template <bool INV, int E>
+__device__ __forceinline__ void bfly_folded(double2& e, double2& o) {
+    using W = W16Fold<INV, E>;
+    const double2 c = fold_w16<INV, E>(o);
+    o = make_double2(fma(-W::m, c.x, e.x), fma(-W::m, c.y, e.y));
+    e = make_double2(fma(W::m, c.x, e.x), fma(W::m, c.y, e.y));
+}
+template <bool INV> struct RegDft<double2, 8, INV> {
+    __device__ static __forceinline__ void run(double2* v) {
+        double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+        dft4<double2, INV>(e0, e1, e2, e3);
+        dft4<double2, INV>(o0, o1, o2, o3);
+        o2 = mul_w16<double2, INV, 4>(o2);
+        v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+        v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+        bfly_folded<INV, 2>(e1, o1);
+        bfly_folded<INV, 6>(e3, o3);
+        v[1] = e1; v[5] = o1;
+        v[3] = e3; v[7] = o3;
+    }
+};
+template <bool INV> struct RegDft<double2, 16, INV> {
+    __device__ static __forceinline__ void run(double2* v) {
+#pragma unroll
+        for (int j1 = 0; j1 < 4; ++j1) dft4<double2, INV>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12]);
+        // row k2 holds v[4 k2 + j1], j1 = 0..3, whose twiddle is W16^{j1 k2}
+        double2 r[16];
+        {
+            double2 a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+            dft4<double2, INV>(a0, a1, a2, a3);
+            r[0] = a0; r[4] = a1; r[8] = a2; r[12] = a3;
+        }
+        {
+            double2 a0 = v[4], a1 = v[5], a2 = v[6], a3 = v[7];
+            dft4_folded<INV, 1>(a0, a1, a2, a3);
+            r[1] = a0; r[5] = a1; r[9] = a2; r[13] = a3;
+        }
+        {
+            double2 a0 = v[8], a1 = v[9], a2 = v[10], a3 = v[11];
+            dft4_folded<INV, 2>(a0, a1, a2, a3);
+            r[2] = a0; r[6] = a1; r[10] = a2; r[14] = a3;
+        }
+        {
+            double2 a0 = v[12], a1 = v[13], a2 = v[14], a3 = v[15];
+            dft4_folded<INV, 3>(a0, a1, a2, a3);
+            r[3] = a0; r[7] = a1; r[11] = a2; r[15] = a3;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = r[i];
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Two-level FFT of length N = N1 N2 (N <= 256): with j = j1 + N1 j2 and
 // k = k2 + N2 k1,
