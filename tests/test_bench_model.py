@@ -6,6 +6,7 @@ their own (the inverse x transform before them is a separate launch), so their
 flops are the per-point counts only; DRAM bytes are the compulsory reads and
 writes of each launch in units of one field S and of the potential S_V."""
 import math
+import sys
 
 import pytest
 
@@ -84,3 +85,23 @@ def test_cpu_sample_slab_of_large_grids():
     assert np.array_equal(W.potential(ws), W.potential(w)[120:136])
     small = bench.workload("spin2_2d")
     assert bench.cpu_workload_sample(small)[0] is small
+
+
+def test_grid_option_is_an_evaluation_rate_only_run(monkeypatch):
+    # --grid runs the workload's problem on another grid (small profiling cases): no
+    # solves and no CPU baseline; the batched sweep has no single grid to change
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--grid", "128,128,256", "--precision", "mixed"])
+    a = bench.parse()
+    assert a.grid == "128,128,256" and a.no_solve and a.no_cpu_baseline
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", "batch512", "--grid", "64,64"])
+    with pytest.raises(SystemExit):
+        bench.parse()
+
+
+def test_stored_oracle_ground_states_are_read_by_name():
+    # the bench's time-to-ground-state entries compare with these stored energies
+    assert bench.golden_ground_state("spin2_2d_256x256") == pytest.approx(19.227438467888131, rel=1e-15)
+    assert bench.golden_ground_state("spin3_3d_128cubed") == pytest.approx(4.826029455710223, rel=1e-15)
+    assert bench.golden_ground_state("no_such_workload") is None
+    r = bench.gold_report(2.0, {"fp64": 2.0 + 2e-12})
+    assert r["energy"] == 2.0 and r["fp64_rel_err"] == pytest.approx(1e-12)
