@@ -5,7 +5,8 @@ only the oracle and the seeded input generators).
 Each case is solved by the oracle's own Algorithm 1 (RGBB warm start, ARNT) to
 the workload's tolerance (1e-8 on ||grad||; 1e-10 for the spin-1 1D case), from
 the seeded initial data of the workload, cascadically where the workload lists
-coarse levels.  The batched spin-1 sweep is represented by a seeded stratified
+coarse levels (the spin-2 2D workload also cascadically from n/4 and n/2, as a
+second case).  The batched spin-1 sweep is represented by a seeded stratified
 sample of three instances per grid size.  The 256^3 spin-3 workload is not
 solved here: the oracle's step on it takes minutes, its solve days.
 
@@ -44,8 +45,11 @@ def batch_sample(count_per_class=3):
 
 def cases():
     from paper_1907_01194_gb300 import workloads as W
+    from dataclasses import replace
     cs = {"spin1_1d_n256": (W.spin1_1d(), 1e-10),
           "spin2_2d_256x256": (W.spin2_2d(), 1e-8),
+          # the same problem by Algorithm 1's cascade from the levels n/4, n/2
+          "spin2_2d_256x256_cascadic": (replace(W.spin2_2d(), levels=((64, 64), (128, 128))), 1e-8),
           "spin3_3d_128cubed": (W.spin3_3d_cascadic(), 1e-8)}
     insts = W.batched_spin1_2d()
     for i in batch_sample():

@@ -67,6 +67,44 @@ def test_direct_ground_state_matches_oracle(wname, tol, dev):
         assert abs(N[0] - 1) < 1e-12 and abs(Mg[0] - w.M) < 1e-12
 
 
+def _row(name):
+    # the stored row's key=value fields (iteration counts of the oracle's finest level)
+    for r in golden("baseline_ground_states.txt"):
+        if r[0] == name:
+            return dict(f.split("=", 1) for f in r[3:] if "=" in f)
+    pytest.skip(f"no oracle ground state stored for {name}")
+
+
+def test_spin2_2d_by_algorithm_1_reaches_the_oracle_ground_state(dev):
+    # the same 256^2 spin-2 problem solved by Algorithm 1's cascade (levels n/4, n/2):
+    # the oracle's single-mesh ground state (1e-10 FP64, 1e-7 mixed) with a handful of
+    # finest-level Newton iterations instead of the single-mesh solve's ~100, and the
+    # oracle's own cascade taking the same number of them
+    from paper_1907_01194_gb300 import sbec
+    w = W.spin2_2d()
+    E_or = _need(w.name)
+    assert abs(_need("spin2_2d_256x256_cascadic") - E_or) <= 1e-13 * abs(E_or)
+    row = _row("spin2_2d_256x256_cascadic")
+    lv = [w.at((64, 64)), w.at((128, 128)), w]
+    h64 = [sbec.Handle.from_workload(x) for x in lv]
+    h32 = [sbec.Handle.from_workload(x, precision="mixed") for x in lv]
+
+    def states():
+        return [torch.from_numpy(W.initial_fields(lv[0])).to(dev)] + [
+            torch.empty((x.C,) + x.shape, dtype=torch.complex128, device=dev) for x in lv[1:]]
+    try:
+        st = sbec.solve_cascadic(h64, states(), tol=1e-8)
+        sm, sf = sbec.solve_cascadic_mixed(h64, h32, states(), tol=1e-8)
+    finally:
+        for h in h64 + h32:
+            h.close()
+    assert st["converged"] and st["outer_iters"] <= 30, st
+    assert st["outer_iters"] == int(row["outer"]), (st, row)
+    assert abs(st["inner_iters"] - int(row["inner"])) <= 0.1 * int(row["inner"]), (st, row)
+    assert abs(st["energy"] - E_or) <= 1e-10 * abs(E_or), (st["energy"], E_or)
+    assert sf["converged"] and abs(sf["energy"] - E_or) <= 1e-7 * abs(E_or), (sf["energy"], E_or)
+
+
 def test_cascadic_spin3_128_matches_oracle(dev):
     from paper_1907_01194_gb300 import sbec
     w = W.spin3_3d_cascadic()
