@@ -10,7 +10,10 @@ stratified sample the script solves (three instances per grid size), each
 solved here in a batch of the sampled instances of its size.  The 256^3 spin-3
 workload is beyond the oracle's reach as a solve; its GPU ground state is
 checked by the oracle's own energy and gradient evaluated at the returned state
-(a property of a ground state that holds at any size)."""
+(a property of a ground state that holds at any size).  The cascadic solves
+(the 128^3 spin-3 workload, and the 256^2 spin-2 workload by Algorithm 1 from
+n/4 and n/2) also take the oracle's number of finest-level Newton iterations,
+and its CG iterations to 10%."""
 import numpy as np
 import pytest
 
@@ -127,6 +130,10 @@ def test_cascadic_spin3_128_matches_oracle(dev):
     assert st["converged"] and sf["converged"]
     assert abs(st["energy"] - E_or) <= 1e-10 * abs(E_or), (st["energy"], E_or)
     assert abs(sf["energy"] - E_or) <= 1e-7 * abs(E_or), (sf["energy"], E_or)
+    # the finest level's Newton and CG iterations as the oracle's cascade took them
+    row = _row(w.name)
+    assert st["outer_iters"] == int(row["outer"]), (st, row)
+    assert abs(st["inner_iters"] - int(row["inner"])) <= 0.1 * int(row["inner"]), (st, row)
 
 
 def test_batch_sample_matches_oracle(dev):
