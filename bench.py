@@ -80,6 +80,10 @@ NCU_TRAFFIC = {
     # 128^3 capture of the same kernel (mean over its 8 launches, both forms) scaled by the
     # 8x larger fields (writes partly held in L2 at 128^3, so this is a lower bound at 256^3)
     ("proj_apply", "spin3_3d_256cubed", "mixed"): 8 * (234989280.0 + 81436448.0),
+    # 128^3 capture of the FP64 spin-3 Hessian epilogue that reads the stored densities
+    # (reads 994.2 MB, writes 241.7 MB per launch: 4 S + S_V + 16 density doubles per point)
+    # scaled by the 8x larger fields
+    ("x_inv_hess", "spin3_3d_256cubed", "fp64"): 8 * (994229760.0 + 241698048.0),
 }
 
 
